@@ -1,0 +1,269 @@
+/*
+ * fdwave.h - C ABI of the GB300 shaped-stencil acoustic wave library
+ * (libfdwave.so, built for sm_103a).
+ *
+ * The library advances the constant-density acoustic wave equation with a
+ * damping (sponge) term,
+ *     u_tt + eta(x) u_t - c(x)^2 Lap u = f(x, t)            (paper Eq. wave_eq
+ *                                                             and Section 3.1)
+ * with the centred second-order leapfrog in time (Eq. time_derivative1) and a
+ * symmetric shaped Laplacian stencil of radius M in space
+ * (Eq. spacexz_derivative2_sym; shapes of Section 4.1; weight schemes of
+ * Sections 3.3-3.4), on a regular grid of spacing h and time step tau.
+ *
+ * Discrete step on the padded grid (field zero outside it):
+ *   u^{n+1} = [2 u^n - (1 - g) u^{n-1} + k * sum_o a_o u^n(x + o) + a_src^n] / (1 + g)
+ * with k = (c tau / h)^2 per node, g = eta tau / 2, a_o the orbit weights
+ * (the Laplacian is h^-2 sum_o a_o u(x+o)), a_src^n = tau^2 s(t^n) / h^dim at
+ * a source node.  Traces: trace[n][r] = u^{n+1} at receiver r.
+ *
+ * Conventions for every call:
+ *   - Layout: 2D arrays are [z][x], 3D arrays are [z][y][x], x contiguous,
+ *     row-major, FP32 unless stated.  "Physical" arrays have the problem's
+ *     n[] nodes per axis; "padded" arrays have n[] + 2 nb nodes per axis.
+ *   - Indices of sources/receivers are linear row-major indices into the
+ *     physical grid, int64, HOST memory.
+ *   - Pointers suffixed _d are device pointers (cudaMalloc'd or torch
+ *     tensors); the caller owns all memory.  The library never allocates
+ *     device memory except where a call says so: scratch comes from a
+ *     caller-provided workspace of the size the *_workspace_size call gives,
+ *     256-byte aligned.
+ *   - All device work is enqueued on the caller's stream (a cudaStream_t,
+ *     NULL for the legacy default stream) and is asynchronous; host-side
+ *     argument errors are reported synchronously.
+ *   - Errors: every call returns an fd_status; nothing is thrown across the
+ *     ABI.  fd_last_error() gives a thread-local message for the last failing
+ *     call of the calling thread.  Conditions detected on the device (time-out
+ *     of a bounded wait, a velocity above vmax) are recorded in a status word
+ *     in the workspace and returned by fd_status_read().
+ */
+#ifndef FDWAVE_H
+#define FDWAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FD_OK = 0,
+    FD_ERR_ARG = -1,          /* invalid argument (message in fd_last_error) */
+    FD_ERR_CUDA = -2,         /* a CUDA runtime/driver call failed */
+    FD_ERR_UNSTABLE = -3,     /* dt above the von Neumann limit, or vmax exceeded */
+    FD_ERR_SINGULAR = -4,     /* weight system singular / not solvable */
+    FD_ERR_TIMEOUT = -5,      /* a bounded device wait expired (kernel returned early) */
+    FD_ERR_NOMEM = -6,        /* workspace too small or host allocation failed */
+    FD_ERR_UNSUPPORTED = -7   /* combination not implemented */
+} fd_status;
+
+/* Stencil shapes of Section 4.1 (3D: union of the 2D shape in the three
+ * coordinate planes). */
+typedef enum {
+    FD_CROSS = 0,             /* axes only, 4M+1 points (2D) */
+    FD_CROSS_RHOMBUS = 1,     /* axes to M plus {|p|+|q| <= N} */
+    FD_RHOMBUS = 2,           /* {|p|+|q| <= M} */
+    FD_CROSS_SQUARE = 3,      /* axes to M plus {min(|p|,|q|) <= N, max <= M} */
+    FD_SQUARE = 4             /* {max(|p|,|q|) <= M} */
+} fd_shape;
+
+/* Weight schemes of Sections 3.3 (spatial) and 3.4 (dispersion-based). */
+typedef enum {
+    FD_SPATTE = 0,            /* Taylor, Eq. taylor_system (off-axis weights 0) */
+    FD_SPECTE_THETA = 1,      /* polar Taylor at angle theta, Eqs. taylor_system_r*_spec */
+    FD_SPECLS = 2,            /* least squares of the spatial symbol, Section 3.3.3 */
+    FD_DISPTE = 3,            /* time-space Taylor, Eqs. taylor_system_r*_disp */
+    FD_DISPTE_THETA = 4,      /* polar variant at angle theta, Eqs. *_disp_theta */
+    FD_DISPLS = 5             /* least squares of the dispersion relation, Section 3.4.3 */
+} fd_scheme;
+
+/* Basis of the least-squares schemes: the one the paper adopts (Taylor basis
+ * for SpecLS, Eq. taylor_laplacian_spec_disp_linsys; cosine basis for DispLS,
+ * Eq. displs_cont_linsys), or either basis explicitly. */
+typedef enum { FD_LS_PAPER = 0, FD_LS_TAYLOR = 1, FD_LS_COSINE = 2 } fd_ls_basis;
+
+typedef struct {
+    int32_t dim;              /* 2 or 3 */
+    int32_t shape;            /* fd_shape */
+    int32_t M;                /* radius, 1 <= M <= 16 */
+    int32_t N;                /* inner size of CROSS_RHOMBUS (1..M) / CROSS_SQUARE (0..M) */
+    int32_t scheme;           /* fd_scheme */
+    int32_t ls_basis;         /* fd_ls_basis (LS schemes only) */
+    double courant;           /* C = c_max tau / h for the Disp* schemes (Eq. courant) */
+    double theta;             /* wave-number angle of the *_THETA schemes (2D only) */
+    double band;              /* LS band: beta = k h in [0, band]; <= 0 selects pi/2 */
+} fd_stencil_desc;
+
+/* Maximum number of orbits any supported stencil has. */
+#define FD_MAX_ORBITS 160
+
+/*
+ * fd_weights - stencil weights, one per symmetry orbit (HOST, FP64, pure).
+ * Orbits are keyed by sorted absolute offsets (p >= q >= s >= 0; s = 0 in
+ * 2D); orbit 0 is the centre.  mult[i] is the orbit's number of offsets.
+ *   desc      stencil description
+ *   cap       capacity of the output arrays (>= number of orbits)
+ *   n_orbits  out: number of orbits written
+ *   orbits    out: [cap][3] (p, q, s)
+ *   mult      out: [cap]
+ *   w         out: [cap] weights a (the Laplacian is h^-2 sum a u)
+ * Errors: FD_ERR_ARG (bad desc or cap), FD_ERR_SINGULAR, FD_ERR_UNSUPPORTED
+ * (theta schemes in 3D).
+ */
+int fd_weights(const fd_stencil_desc *desc, int cap, int *n_orbits,
+               int32_t *orbits, int32_t *mult, double *w);
+
+/*
+ * fd_cfl_limit - von Neumann stability limit of the leapfrog with this
+ * stencil: C_max = 2 / sqrt(max_k -S(k)), S(k) = sum_o a_o cos(k.o) (the
+ * symbol in Eq. full_disp).  A run is stable when c_max tau / h <= C_max.
+ * HOST, FP64.  Errors: as fd_weights.
+ */
+int fd_cfl_limit(const fd_stencil_desc *desc, double *courant_max);
+
+/*
+ * fd_ricker - Ricker wavelet s(t^n), t^n = n dt, n = 0..nt-1, with peak
+ * frequency f0 and delay 1/f0 (the source named in Section 3.1):
+ * s(t) = (1 - 2 pi^2 f0^2 (t - 1/f0)^2) exp(-pi^2 f0^2 (t - 1/f0)^2).
+ * out: HOST float[nt].  Errors: FD_ERR_ARG.
+ */
+int fd_ricker(double f0, double dt, int nt, float *out);
+
+/* Problem on the physical grid; the sponge of nb nodes is added per side. */
+typedef struct {
+    int32_t dim;              /* 2 or 3 */
+    int32_t nb;               /* sponge width in nodes (>= 0) */
+    int64_t n[3];             /* physical nodes (nz, ny, nx); ny = 1 in 2D */
+    int32_t nt;               /* number of time steps */
+    int32_t reserved;
+    double h;                 /* grid spacing (m) */
+    double dt;                /* time step tau (s) */
+    double vmax;              /* largest velocity of any model used (m/s) */
+    double damp_R;            /* sponge reflection target R (<= 0 selects 1e-3):
+                                 eta(d) = eta_max (d/nb)^2 summed over axes,
+                                 eta_max = 3 vmax ln(1/R) / (2 nb h) */
+} fd_problem;
+
+typedef struct fd_plan fd_plan;
+
+/* Model parameterisation of the model_d arrays. */
+typedef enum { FD_MODEL_VELOCITY = 0, FD_MODEL_SLOWNESS2 = 1 } fd_model_kind;
+
+/*
+ * fd_plan_create - validate a problem and stencil, solve the weights (host
+ * FP64, rounded to FP32 for the kernels), check vmax dt / h <= C_max
+ * (FD_ERR_UNSTABLE otherwise) and choose the kernel variant.  The plan owns
+ * only host memory.  Errors: FD_ERR_ARG, FD_ERR_UNSTABLE, FD_ERR_SINGULAR,
+ * FD_ERR_UNSUPPORTED, FD_ERR_NOMEM.
+ */
+int fd_plan_create(const fd_problem *prob, const fd_stencil_desc *stencil, fd_plan **out);
+void fd_plan_destroy(fd_plan *plan);
+
+typedef struct {
+    int64_t padded[3];        /* padded nodes per axis (nz, ny, nx) */
+    int64_t pitch;            /* row pitch (floats) of the internal field buffers */
+    int32_t n_orbits;         /* orbits of the stencil (after zero-weight reduction) */
+    int32_t kernel;           /* kernel variant id chosen by the plan */
+    double courant_max;       /* fd_cfl_limit of the stencil */
+    int32_t tile[3];          /* tile (x, y/z, z-chunk) of the chosen variant */
+    int32_t effective_shape;  /* shape after dropping all-zero off-axis orbits */
+} fd_plan_info;
+int fd_plan_get_info(const fd_plan *plan, fd_plan_info *info);
+
+/*
+ * fd_forward_workspace_size - bytes of device workspace fd_forward needs for
+ * nsrc sources and nrec receivers (three padded field buffers, tile-bucketed
+ * source/receiver tables, the status word).
+ */
+int fd_forward_workspace_size(const fd_plan *plan, int nsrc, int nrec, size_t *bytes);
+
+/*
+ * fd_forward - run the plan's nt steps from u^0 = u^{-1} = 0 (or a given
+ * state), injecting sources and recording traces (Section 3.1, Data objects of
+ * Section 5.2).
+ *   model_kind  fd_model_kind of model_d
+ *   model_d     physical [nz][ny][nx] velocity (m/s) or slowness squared m = 1/v^2
+ *   nsrc, src_idx    sources: HOST int64 physical linear indices
+ *   wavelet_d   [nt][nsrc] source time functions s(t^n) (e.g. fd_ricker)
+ *   nrec, rec_idx    receivers: HOST int64 physical linear indices
+ *   traces_d    out [nt][nrec]: u^{n+1} at the receivers (may be NULL if nrec = 0)
+ *   state_in_d  NULL for zero initial state, else padded [2][..] = (u^0, u^{-1})
+ *   state_out_d NULL, or out padded [2][..] = (u^{nt}, u^{nt-1})
+ *   ws_d, ws_bytes   workspace (>= fd_forward_workspace_size)
+ *   stream      cudaStream_t
+ * The model's maximum must not exceed the plan's vmax; a larger value is
+ * recorded in the status word (FD_ERR_UNSTABLE from fd_status_read).
+ */
+int fd_forward(fd_plan *plan, int model_kind, const float *model_d,
+               int nsrc, const int64_t *src_idx, const float *wavelet_d,
+               int nrec, const int64_t *rec_idx, float *traces_d,
+               const float *state_in_d, float *state_out_d,
+               void *ws_d, size_t ws_bytes, void *stream);
+
+/*
+ * fd_status_read - synchronise `stream` and return the device status word of
+ * the last call that used workspace ws_d (FD_OK, FD_ERR_TIMEOUT,
+ * FD_ERR_UNSTABLE), then clear it.
+ */
+int fd_status_read(const fd_plan *plan, void *ws_d, void *stream);
+
+/*
+ * fd_gradient_workspace_size / fd_adjoint_gradient - gradient of a misfit
+ * J(traces) with respect to m = 1/v^2 on the physical grid by the exact
+ * discrete adjoint of the step above (the paper names FWI as the target use,
+ * Section 1 and 7; the adjoint is derived from the discrete step).
+ *   resid_d     [nt][nrec] dJ/dtrace (for J = 1/2 ||d - d_obs||^2: d - d_obs)
+ *   ckpt_every  k >= 1: the forward sweep stores (u^n, u^{n-1}) every k steps;
+ *               the backward sweep recomputes each segment of k steps and runs
+ *               the adjoint steps over it
+ *   grad_d      out physical [nz][ny][nx] dJ/dm (overwritten)
+ *   traces_d    optional out [nt][nrec] traces of the forward sweep (NULL: none)
+ *   wavelet_grad_d  optional out [nt][nsrc] dJ/ds(t^n) for each source, the
+ *               adjoint of the source-injection map (NULL: none)
+ * Other arguments as fd_forward.  Workspace: three field buffers, (2 nt/k)
+ * checkpoint fields, k segment fields and the gradient accumulator.
+ */
+int fd_gradient_workspace_size(const fd_plan *plan, int nsrc, int nrec, int ckpt_every,
+                               size_t *bytes);
+int fd_adjoint_gradient(fd_plan *plan, int model_kind, const float *model_d,
+                        int nsrc, const int64_t *src_idx, const float *wavelet_d,
+                        int nrec, const int64_t *rec_idx, const float *resid_d,
+                        int ckpt_every, float *grad_d, float *traces_d,
+                        float *wavelet_grad_d, void *ws_d, size_t ws_bytes, void *stream);
+
+/*
+ * Batched shots: independent forward problems (possibly on grids of
+ * different size, same stencil, dt and nt) advanced together, one launch per
+ * time step over a tile table spanning all shots, the whole time loop
+ * captured once into a CUDA graph and replayed.  Fields of every shot must
+ * fit the workspace at once.
+ */
+typedef struct {
+    const fd_plan *plan;      /* plan of this shot's grid (shared stencil/dt/nt) */
+    int32_t model_kind;
+    int32_t nsrc;
+    int32_t nrec;
+    int32_t reserved;
+    const float *model_d;
+    const int64_t *src_idx;   /* HOST */
+    const float *wavelet_d;   /* [nt][nsrc] */
+    const int64_t *rec_idx;   /* HOST */
+    float *traces_d;          /* [nt][nrec] */
+} fd_shot;
+
+int fd_forward_batched_workspace_size(int nshots, const fd_shot *shots, size_t *bytes);
+int fd_forward_batched(int nshots, const fd_shot *shots, void *ws_d, size_t ws_bytes,
+                       void *stream);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *fd_last_error(void);
+
+/* Library version string. */
+const char *fd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDWAVE_H */

@@ -18,6 +18,8 @@ from typing import Dict, List, Sequence, Tuple
 
 import numpy as np
 
+LS_RCOND = 1e-10
+
 SHAPES = ("cross", "cross_rhombus", "rhombus", "cross_square", "square")
 SCHEMES = ("spatte", "specte_theta", "specls", "dispte", "dispte_theta", "displs")
 
@@ -295,7 +297,11 @@ def ls_weights(dim: int, orbs, M: int, scheme: str, C: float, b: float,
 
     Inner product (Eq. cont_dotprod): integral over beta in [0, b] (Gauss-
     Legendre) and over all directions (2D: theta in [0, 2 pi]; 3D: the unit
-    sphere).  Solved as a minimum-norm least-squares problem."""
+    sphere).  Solved as the minimum-norm least-squares problem (Section 4.2,
+    third bullet) with singular values below LS_RCOND * sigma_max dropped: the
+    design matrices are ill-conditioned (up to ~1e13 for Square(8)) with no
+    spectral gap, and a fixed relative cutoff makes the solution well defined
+    to ~1e-6 independent of the solver."""
     if basis == "paper":
         basis = "taylor" if scheme == "specls" else "cosine"
     keys = [k for k in orbs.keys() if any(k)]
@@ -324,7 +330,7 @@ def ls_weights(dim: int, orbs, M: int, scheme: str, C: float, b: float,
         Phi = Phi / target[:, None]
         target = np.ones_like(target)
     sw = np.sqrt(W)
-    a, *_ = np.linalg.lstsq(Phi * sw[:, None], target * sw, rcond=None)
+    a, *_ = np.linalg.lstsq(Phi * sw[:, None], target * sw, rcond=LS_RCOND)
     w = {k: float(v) for k, v in zip(keys, a)}
     center = tuple([0] * dim)
     w[center] = -sum(len(orbs[k]) * w[k] for k in keys)

@@ -1,0 +1,340 @@
+"""GB300 shaped-stencil acoustic wave engine: Python binding of libfdwave.
+
+Thin ctypes layer over the C ABI declared in ``include/fdwave.h``; the names
+match the C entry points (``fd_weights``, ``fd_forward``, ...).  PyTorch
+supplies device memory and streams only; every step of the time loop runs in
+the library's CUDA kernels.  There is no CPU fallback: if the shared library
+is missing or no GPU is present, the device calls raise.
+
+The ``Plan`` helper and ``AcousticTraces`` (a ``torch.autograd.Function``
+mapping m = 1/v^2 to receiver traces, with the exact discrete adjoint as its
+backward) are conveniences built only from those entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import enum
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfdwave.so")
+
+# ----------------------------------------------------------------------------
+# enums and structs (mirror include/fdwave.h)
+# ----------------------------------------------------------------------------
+FD_OK, FD_ERR_ARG, FD_ERR_CUDA, FD_ERR_UNSTABLE = 0, -1, -2, -3
+FD_ERR_SINGULAR, FD_ERR_TIMEOUT, FD_ERR_NOMEM, FD_ERR_UNSUPPORTED = -4, -5, -6, -7
+
+SHAPES = {"cross": 0, "cross_rhombus": 1, "rhombus": 2, "cross_square": 3, "square": 4}
+SCHEMES = {"spatte": 0, "specte_theta": 1, "specls": 2, "dispte": 3, "dispte_theta": 4,
+           "displs": 5}
+LS_BASIS = {"paper": 0, "taylor": 1, "cosine": 2}
+FD_MODEL_VELOCITY, FD_MODEL_SLOWNESS2 = 0, 1
+FD_MAX_ORBITS = 160
+
+
+class fd_stencil_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("shape", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("N", ctypes.c_int32), ("scheme", ctypes.c_int32), ("ls_basis", ctypes.c_int32),
+                ("courant", ctypes.c_double), ("theta", ctypes.c_double),
+                ("band", ctypes.c_double)]
+
+
+class fd_problem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("nb", ctypes.c_int32), ("n", ctypes.c_int64 * 3),
+                ("nt", ctypes.c_int32), ("reserved", ctypes.c_int32), ("h", ctypes.c_double),
+                ("dt", ctypes.c_double), ("vmax", ctypes.c_double), ("damp_R", ctypes.c_double)]
+
+
+class fd_plan_info(ctypes.Structure):
+    _fields_ = [("padded", ctypes.c_int64 * 3), ("pitch", ctypes.c_int64),
+                ("n_orbits", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("courant_max", ctypes.c_double), ("tile", ctypes.c_int32 * 3),
+                ("effective_shape", ctypes.c_int32)]
+
+
+class fd_shot(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("model_kind", ctypes.c_int32),
+                ("nsrc", ctypes.c_int32), ("nrec", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("model_d", ctypes.c_void_p), ("src_idx", ctypes.c_void_p),
+                ("wavelet_d", ctypes.c_void_p), ("rec_idx", ctypes.c_void_p),
+                ("traces_d", ctypes.c_void_p)]
+
+
+class FdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("fdwave error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+_P, _I, _I64, _D, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+_SIGS = {
+    "fd_weights": (_I, [_P, _I, _P, _P, _P, _P]),
+    "fd_cfl_limit": (_I, [_P, _P]),
+    "fd_ricker": (_I, [_D, _D, _I, _P]),
+    "fd_plan_create": (_I, [_P, _P, _P]),
+    "fd_plan_destroy": (None, [_P]),
+    "fd_plan_get_info": (_I, [_P, _P]),
+    "fd_forward_workspace_size": (_I, [_P, _I, _I, _P]),
+    "fd_forward": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
+    "fd_status_read": (_I, [_P, _P, _P]),
+    "fd_gradient_workspace_size": (_I, [_P, _I, _I, _I, _P]),
+    "fd_adjoint_gradient": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _P, _P, _SZ, _P]),
+    "fd_forward_batched_workspace_size": (_I, [_I, _P, _P]),
+    "fd_forward_batched": (_I, [_I, _P, _P, _SZ, _P]),
+    "fd_last_error": (ctypes.c_char_p, []),
+    "fd_version": (ctypes.c_char_p, []),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libfdwave.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfdwave.so is not built (run __graft_entry__.build() or "
+                               "python -m paper_2606_04882_gb300.build); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().fd_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != FD_OK:
+        raise FdError(rc, last_error())
+
+
+def _addr(x) -> Optional[int]:
+    """Device/host address of a tensor/array (None for None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x)
+
+
+# ----------------------------------------------------------------------------
+# host entry points
+# ----------------------------------------------------------------------------
+
+def stencil_desc(dim: int, shape: str = "cross", M: int = 4, N: int = 0, scheme: str = "spatte",
+                 courant: float = 0.0, theta: float = np.pi / 8, band: float = np.pi / 2,
+                 ls_basis: str = "paper") -> fd_stencil_desc:
+    return fd_stencil_desc(dim, SHAPES[shape], M, N, SCHEMES[scheme], LS_BASIS[ls_basis],
+                           courant, theta, band)
+
+
+def fd_weights(desc: fd_stencil_desc):
+    """Orbit keys [n, 3], multiplicities [n] and FP64 weights [n]."""
+    n = ctypes.c_int(0)
+    keys = np.zeros((FD_MAX_ORBITS, 3), np.int32)
+    mult = np.zeros(FD_MAX_ORBITS, np.int32)
+    w = np.zeros(FD_MAX_ORBITS, np.float64)
+    _check(lib().fd_weights(ctypes.byref(desc), FD_MAX_ORBITS, ctypes.byref(n), keys.ctypes.data,
+                            mult.ctypes.data, w.ctypes.data))
+    k = n.value
+    return keys[:k].copy(), mult[:k].copy(), w[:k].copy()
+
+
+def fd_cfl_limit(desc: fd_stencil_desc) -> float:
+    c = ctypes.c_double(0.0)
+    _check(lib().fd_cfl_limit(ctypes.byref(desc), ctypes.byref(c)))
+    return c.value
+
+
+def fd_ricker(f0: float, dt: float, nt: int) -> np.ndarray:
+    out = np.zeros(nt, np.float32)
+    _check(lib().fd_ricker(f0, dt, nt, out.ctypes.data))
+    return out
+
+
+def fd_version() -> str:
+    return lib().fd_version().decode()
+
+
+# ----------------------------------------------------------------------------
+# plans and device calls (torch supplies memory and streams)
+# ----------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class Plan:
+    """Owns an fd_plan (host only).  ``shape`` is the physical grid (nz, nx) or
+    (nz, ny, nx)."""
+
+    def __init__(self, shape: Sequence[int], h: float, dt: float, nt: int, nb: int, vmax: float,
+                 stencil: fd_stencil_desc, damp_R: float = 0.0):
+        dim = len(shape)
+        n = (shape[0], 1, shape[1]) if dim == 2 else tuple(shape)
+        self.prob = fd_problem(dim, nb, (ctypes.c_int64 * 3)(*n), nt, 0, h, dt, vmax, damp_R)
+        self.stencil = stencil
+        self.shape = tuple(shape)
+        self.dim, self.nb, self.nt, self.h, self.dt = dim, nb, nt, h, dt
+        p = ctypes.c_void_p(0)
+        _check(lib().fd_plan_create(ctypes.byref(self.prob), ctypes.byref(stencil), ctypes.byref(p)))
+        self.ptr = p
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.fd_plan_destroy(self.ptr)
+            self.ptr = None
+
+    def info(self) -> fd_plan_info:
+        inf = fd_plan_info()
+        _check(lib().fd_plan_get_info(self.ptr, ctypes.byref(inf)))
+        return inf
+
+    @property
+    def padded_shape(self):
+        inf = self.info()
+        p = tuple(inf.padded)
+        return (p[0], p[2]) if self.dim == 2 else p
+
+    def forward_workspace_size(self, nsrc: int, nrec: int) -> int:
+        b = ctypes.c_size_t(0)
+        _check(lib().fd_forward_workspace_size(self.ptr, nsrc, nrec, ctypes.byref(b)))
+        return b.value
+
+    def gradient_workspace_size(self, nsrc: int, nrec: int, k: int) -> int:
+        b = ctypes.c_size_t(0)
+        _check(lib().fd_gradient_workspace_size(self.ptr, nsrc, nrec, k, ctypes.byref(b)))
+        return b.value
+
+    def linear_index(self, pos) -> np.ndarray:
+        pos = np.atleast_2d(np.asarray(pos, np.int64))
+        if self.dim == 2:
+            return (pos[:, 0] * self.shape[1] + pos[:, 1]).astype(np.int64)
+        return ((pos[:, 0] * self.shape[1] + pos[:, 1]) * self.shape[2] + pos[:, 2]).astype(np.int64)
+
+
+def workspace(nbytes: int, device="cuda"):
+    """A 256-byte aligned device workspace (torch allocation)."""
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def fd_forward(plan: Plan, model, src_idx: np.ndarray, wavelet, rec_idx: np.ndarray, traces,
+               ws, state_in=None, state_out=None, model_kind: int = FD_MODEL_VELOCITY,
+               stream=None):
+    """Enqueue the forward run (all tensors on the device, indices on the host)."""
+    src_idx = np.ascontiguousarray(src_idx, np.int64)
+    rec_idx = np.ascontiguousarray(rec_idx, np.int64)
+    _check(lib().fd_forward(plan.ptr, model_kind, _addr(model), len(src_idx),
+                            src_idx.ctypes.data if len(src_idx) else None, _addr(wavelet),
+                            len(rec_idx), rec_idx.ctypes.data if len(rec_idx) else None,
+                            _addr(traces), _addr(state_in), _addr(state_out), _addr(ws),
+                            ws.numel(), _stream_ptr(stream)))
+
+
+def fd_status_read(plan: Plan, ws, stream=None) -> int:
+    return lib().fd_status_read(plan.ptr, _addr(ws), _stream_ptr(stream))
+
+
+def fd_adjoint_gradient(plan: Plan, model, src_idx, wavelet, rec_idx, resid, k: int, grad, ws,
+                        traces=None, wavelet_grad=None, model_kind: int = FD_MODEL_VELOCITY,
+                        stream=None):
+    src_idx = np.ascontiguousarray(src_idx, np.int64)
+    rec_idx = np.ascontiguousarray(rec_idx, np.int64)
+    _check(lib().fd_adjoint_gradient(plan.ptr, model_kind, _addr(model), len(src_idx),
+                                     src_idx.ctypes.data if len(src_idx) else None,
+                                     _addr(wavelet), len(rec_idx),
+                                     rec_idx.ctypes.data if len(rec_idx) else None, _addr(resid),
+                                     k, _addr(grad), _addr(traces), _addr(wavelet_grad),
+                                     _addr(ws), ws.numel(), _stream_ptr(stream)))
+
+
+def fd_forward_batched(shots: Sequence[dict], ws, stream=None):
+    """shots: dicts with plan, model, src_idx, wavelet, rec_idx, traces
+    (and optional model_kind)."""
+    arr = (fd_shot * len(shots))()
+    keep = []
+    for i, s in enumerate(shots):
+        si = np.ascontiguousarray(s["src_idx"], np.int64)
+        ri = np.ascontiguousarray(s["rec_idx"], np.int64)
+        keep += [si, ri]
+        arr[i] = fd_shot(s["plan"].ptr.value, s.get("model_kind", FD_MODEL_VELOCITY), len(si),
+                         len(ri), 0, _addr(s["model"]), si.ctypes.data, _addr(s["wavelet"]),
+                         ri.ctypes.data, _addr(s["traces"]))
+    _check(lib().fd_forward_batched(len(shots), arr, _addr(ws), ws.numel(), _stream_ptr(stream)))
+
+
+def batched_workspace_size(shots: Sequence[dict]) -> int:
+    arr = (fd_shot * len(shots))()
+    for i, s in enumerate(shots):
+        arr[i] = fd_shot(s["plan"].ptr.value, 0, len(s["src_idx"]), len(s["rec_idx"]), 0,
+                         None, None, None, None, None)
+    b = ctypes.c_size_t(0)
+    _check(lib().fd_forward_batched_workspace_size(len(shots), arr, ctypes.byref(b)))
+    return b.value
+
+
+# ----------------------------------------------------------------------------
+# autograd: m = 1/v^2 -> traces, backward by the discrete adjoint
+# ----------------------------------------------------------------------------
+
+def _make_traces_fn():
+    torch = _torch()
+
+    class AcousticTraces(torch.autograd.Function):
+        """traces = F(m); grad_m = F'(m)^T grad_traces via fd_adjoint_gradient
+        (checkpoints every ``k`` steps, segments recomputed)."""
+
+        @staticmethod
+        def forward(ctx, m, plan, src_idx, wavelet, rec_idx, k):
+            nt = plan.nt
+            traces = torch.empty((nt, len(rec_idx)), dtype=torch.float32, device=m.device)
+            ws = workspace(plan.forward_workspace_size(len(src_idx), len(rec_idx)), m.device)
+            fd_forward(plan, m, src_idx, wavelet, rec_idx, traces, ws,
+                       model_kind=FD_MODEL_SLOWNESS2)
+            ctx.save_for_backward(m, wavelet)
+            ctx.plan, ctx.src_idx, ctx.rec_idx, ctx.k = plan, src_idx, rec_idx, k
+            return traces
+
+        @staticmethod
+        def backward(ctx, grad_traces):
+            m, wavelet = ctx.saved_tensors
+            plan = ctx.plan
+            grad = torch.empty_like(m)
+            ws = workspace(plan.gradient_workspace_size(len(ctx.src_idx), len(ctx.rec_idx), ctx.k),
+                           m.device)
+            fd_adjoint_gradient(plan, m, ctx.src_idx, wavelet, ctx.rec_idx,
+                                grad_traces.contiguous().float(), ctx.k, grad, ws,
+                                model_kind=FD_MODEL_SLOWNESS2)
+            return grad, None, None, None, None, None
+
+    return AcousticTraces
+
+
+_traces_fn = None
+
+
+def acoustic_traces(m, plan: Plan, src_idx, wavelet, rec_idx, k: int = 20):
+    """Differentiable traces(m) for m = 1/v^2 on the physical grid."""
+    global _traces_fn
+    if _traces_fn is None:
+        _traces_fn = _make_traces_fn()
+    return _traces_fn.apply(m, plan, np.asarray(src_idx, np.int64), wavelet,
+                            np.asarray(rec_idx, np.int64), k)

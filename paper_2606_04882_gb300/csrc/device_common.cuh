@@ -1,0 +1,141 @@
+// Device helpers: shape geometry, shared-memory barriers and TMA copies
+// (inline PTX, sm_100-family), bounded waits, damping.
+#pragma once
+
+#include <cstdint>
+
+#include "internal.h"
+
+namespace fdw {
+
+// ---------------------------------------------------------------------------
+// Stencil geometry (Section 4.1).  ext(q) = largest |p| of a point (p, q) of
+// the 2D shape on row offset |q| (-1: no point besides none; the axis point
+// (0, q) always exists for q <= M).  3D shapes are the union of the 2D shape
+// in the three coordinate planes, so the same function drives them.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int shape_ext(int shape, int M, int N, int q)
+{
+    return q == 0 ? M
+         : q > M ? -1
+         : shape == FD_CROSS ? 0
+         : shape == FD_RHOMBUS ? M - q
+         : shape == FD_SQUARE ? M
+         : shape == FD_CROSS_RHOMBUS ? (q < N ? N - q : 0)
+         : /* FD_CROSS_SQUARE */ (q <= N ? M : N);
+}
+
+__host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
+
+// ---------------------------------------------------------------------------
+// mbarrier + TMA (PTX ISA 8.x, sm_90+; used here on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait with a time bound of about `cycles` SM clocks; false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long cycles = 4000000000LL)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > cycles) return false;
+        __nanosleep(64);
+    }
+}
+
+// 2D tile load: box at (x, y) of the map into dst; completes on `bar`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// 3D tile load: box at (x, y, z).
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Damping: squared node distance into the sponge along one axis.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float layer_d2(int64_t i, int64_t lo, int64_t hi)
+{
+    const int64_t d = i < lo ? lo - i : (i > hi ? i - hi : 0);
+    return static_cast<float>(d * d);
+}
+
+__device__ __forceinline__ float4 ld4(const float *p)
+{
+    return *reinterpret_cast<const float4 *>(p);
+}
+
+__device__ __forceinline__ float4 ldg4(const float *p)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p));
+}
+
+__device__ __forceinline__ float get4(const float4 &v, int j)
+{
+    return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ void add4(float4 &v, int j, float a)
+{
+    v.x += (j == 0) ? a : 0.f;
+    v.y += (j == 1) ? a : 0.f;
+    v.z += (j == 2) ? a : 0.f;
+    v.w += (j == 3) ? a : 0.f;
+}
+
+}  // namespace fdw

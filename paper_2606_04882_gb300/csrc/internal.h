@@ -1,0 +1,130 @@
+// Internal definitions shared by the host runtime (plan.cu) and the kernels.
+// Not part of the ABI (see include/fdwave.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/fdwave.h"
+
+namespace fdw {
+
+constexpr int kMaxM = 16;                    // largest radius of any kernel
+constexpr int kWDim = kMaxM + 1;             // weight table is W[p][q], p,q in [0, M]
+constexpr int kStatusTimeout = 1;            // status word bits
+constexpr int kStatusVmax = 2;
+
+// Point of a per-tile source/receiver table.  Entries of one tile are sorted
+// by z.  (x, y) are local to the tile; z is the padded global plane/row.
+struct PtEntry {
+    int32_t z;
+    int32_t yx;      // (y_local << 16) | x_local
+    int32_t col;     // column in the series / trace row
+    float scale;     // value factor
+};
+
+enum Mode : int {
+    kModeForward = 0,     // plain step: inject sources, sample receivers
+    kModeStoreD = 1,      // forward step that also writes D = kappa * lap to dseg
+    kModeAdjoint = 2      // adjoint step (q-form) with gradient accumulation
+};
+
+// Parameters of one step launch (2D and 3D kernels).
+struct StepParams {
+    const CUtensorMap *tmap;   // tensor map of the field read by the stencil (global memory)
+    float *u_prev;             // in: older field, out: new field (same buffer)
+    const float *kappa;        // (v tau / h)^2 on the padded grid
+    int64_t nx, ny, nz;        // padded sizes (ny = 1 in 2D)
+    int64_t pitch;             // row pitch in floats
+    int64_t plane;             // plane stride in floats (3D)
+    int64_t phys_lo[3];        // first physical node per axis (x, y, z) = nb
+    int64_t phys_hi[3];        // last physical node per axis (x, y, z)
+    float gcoef;               // gamma = gcoef * sum_axes d^2 (d in nodes)
+    int tiles_x, tiles_y;      // tiles per axis (3D: x, y; 2D: x, z)
+    int zchunk;                // 3D: planes per z-chunk
+    int nz_chunks;
+    int step;                  // row of the injection series / sample output
+    // per-tile point tables (CSR over tiles)
+    const int32_t *inj_ptr;
+    const PtEntry *inj;
+    const float *inj_series;
+    int inj_ncol;
+    const int32_t *smp_ptr;
+    const PtEntry *smp;
+    float *smp_out;
+    int smp_ncol;
+    // FWI
+    float *dseg_out;           // kModeStoreD: D written here (same layout as fields)
+    const float *dseg_in;      // kModeAdjoint: D^{j-1}
+    float *gacc;               // kModeAdjoint: accumulator (same layout as fields)
+    int *status;
+    int shot;                  // batched: index into shot tables (unused single-shot)
+    float w[kWDim * kWDim];    // symmetric weight table W[p][q] = a_orbit(max, min)
+};
+
+// Batched 2D: one launch per step over all shots' tiles.
+struct ShotDev {
+    const CUtensorMap *tmap_a, *tmap_b;     // maps of buffers a and b
+    float *buf_a, *buf_b;
+    const float *kappa;
+    int64_t nx, nz, pitch;
+    int64_t phys_lo[2], phys_hi[2];
+    int tiles_x, tiles_z;
+    int tile_base;                          // first global tile id of this shot
+    const int32_t *inj_ptr;
+    const PtEntry *inj;
+    const float *inj_series;
+    int inj_ncol;
+    const int32_t *smp_ptr;
+    const PtEntry *smp;
+    float *smp_out;
+    int smp_ncol;
+};
+
+struct BatchParams {
+    const ShotDev *shots;
+    const int32_t *tile_shot;               // global tile id -> shot
+    int ntiles;
+    int step;                               // time step n (selects buffer parity)
+    float gcoef;
+    int *status;
+    float w[kWDim * kWDim];
+};
+
+// Kernel variant descriptor chosen by the plan.
+struct Variant {
+    int dim, shape, M, N;
+    int generic;       // 1: runtime-M kernel
+    int tx, tz;        // 2D tile: columns, rows of output per CTA; 3D: x, y
+    int threads;
+    size_t smem;
+    int box[3];        // TMA box (x, y, z)
+};
+
+// Host launchers (defined in the .cu files).
+int select_variant_2d(int shape, int M, int N, int64_t nx, int64_t nz, Variant *v);
+int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t nz, Variant *v);
+cudaError_t launch_step2d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
+cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
+cudaError_t launch_batch2d(const Variant &v, const BatchParams &p, int ntiles, cudaStream_t s);
+int batch_supported(const Variant &v);
+
+// aux kernels
+cudaError_t launch_prep_kappa(const float *model, int kind, float *kappa, int dim,
+                              const int64_t phys[3], int nb, const int64_t pad[3],
+                              int64_t pitch, int64_t plane, double dt_over_h,
+                              float vmax_sq_limit, int *status, cudaStream_t s);
+cudaError_t launch_copy_state(const float *src, int64_t src_pitch, int64_t src_plane,
+                              float *dst, int64_t dst_pitch, int64_t dst_plane,
+                              const int64_t pad[3], cudaStream_t s);
+cudaError_t launch_fold_grad(const float *gacc, int64_t pitch, int64_t plane,
+                             const int64_t phys[3], int nb, float scale, float *grad,
+                             cudaStream_t s);
+
+// Driver entry point for cuTensorMapEncodeTiled (resolved at run time).
+int encode_tmap(CUtensorMap *map, const float *base, int rank, const int64_t *dims,
+                const int64_t *strides_bytes, const int *box);
+
+}  // namespace fdw

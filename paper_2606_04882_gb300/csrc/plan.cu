@@ -1,0 +1,769 @@
+// Host runtime of libfdwave: plans, workspace layout, point tables, the
+// forward time loop, the checkpointed adjoint gradient and batched shots.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "runtime.h"
+
+struct fd_plan {
+    fd_problem prob;
+    fd_stencil_desc st;
+    std::vector<std::array<int, 3>> keys;
+    std::vector<int> mult;
+    std::vector<double> w;
+    double cmax = 0.0;
+    int shape_eff = 0;
+    int64_t pad[3] = {1, 1, 1};   // (z, y, x)
+    int64_t pitch = 0, plane = 0, field = 0;   // floats
+    fdw::Variant var{};
+    int tiles_x = 0, tiles_y = 0, ntiles = 0;
+    int zchunk = 0, nz_chunks = 1;
+    bool tuned = false;
+    float gcoef = 0.f;
+    float W[fdw::kWDim * fdw::kWDim];
+    void *last_ws = nullptr;
+};
+
+namespace fdw {
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+constexpr size_t kAlign = 256;
+inline size_t up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+
+#define FDW_CK(call)                                                                     \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return set_error(FD_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+}  // namespace
+
+int set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+namespace {
+
+// ----------------------------- workspace layout ---------------------------
+
+struct Layout {
+    size_t status = 0, tmaps = 0, kappa = 0, buf[4] = {0, 0, 0, 0}, gacc = 0, ckpt = 0, dseg = 0;
+    size_t tab = 0, tab_bytes = 0;
+    size_t total = 0;
+    int n_tmaps = 2, nck = 0, kseg = 0;
+};
+
+struct Tables {
+    std::vector<char> blob;           // host image of the table region
+    size_t inj_ptr = 0, inj = 0, smp_ptr = 0, smp = 0;   // offsets inside blob
+    size_t ainj_ptr = 0, ainj = 0, asmp_ptr = 0, asmp = 0;
+    bool has_adj = false;
+};
+
+size_t table_bytes(const fd_plan *p, int nsrc, int nrec, bool adj)
+{
+    const size_t ptr = up((p->ntiles + 1) * sizeof(int32_t));
+    size_t b = 2 * ptr + up(std::max(nsrc, 1) * sizeof(PtEntry)) + up(std::max(nrec, 1) * sizeof(PtEntry));
+    return adj ? 2 * b : b;
+}
+
+Layout make_layout(const fd_plan *p, int nsrc, int nrec, bool grad, int kseg)
+{
+    Layout L;
+    const size_t fb = up(p->field * sizeof(float));
+    size_t o = 0;
+    L.status = o; o += kAlign;
+    L.n_tmaps = grad ? 4 : 2;
+    L.tmaps = o; o += up(L.n_tmaps * sizeof(CUtensorMap));
+    L.kappa = o; o += fb;
+    for (int i = 0; i < (grad ? 4 : 2); ++i) { L.buf[i] = o; o += fb; }
+    if (grad) {
+        L.gacc = o; o += fb;
+        L.kseg = kseg;
+        L.nck = (p->prob.nt + kseg - 1) / kseg;
+        L.ckpt = o; o += (size_t)2 * L.nck * fb;
+        L.dseg = o; o += (size_t)kseg * fb;
+    }
+    L.tab = o;
+    L.tab_bytes = table_bytes(p, nsrc, nrec, grad);
+    o += L.tab_bytes;
+    L.total = o;
+    return L;
+}
+
+// Map physical linear indices to tile tables (CSR over tiles, z-sorted).
+struct Pt {
+    int tile;
+    PtEntry e;
+};
+
+int locate(const fd_plan *p, int64_t idx, int col, float scale, Pt &out)
+{
+    const fd_problem &pr = p->prob;
+    const int64_t nphys = pr.n[0] * pr.n[1] * pr.n[2];
+    if (idx < 0 || idx >= nphys) return set_error(FD_ERR_ARG, "point index %lld outside the physical grid", (long long)idx);
+    const int64_t ix = idx % pr.n[2], r = idx / pr.n[2], iy = r % pr.n[1], iz = r / pr.n[1];
+    const int64_t x = ix + pr.nb, z = iz + pr.nb, y = pr.dim == 3 ? iy + pr.nb : 0;
+    const int tx = (int)(x / p->var.tx);
+    int tile;
+    int64_t yl;
+    if (pr.dim == 2) {
+        tile = (int)(z / p->var.tz) * p->tiles_x + tx;
+        yl = 0;
+    } else {
+        tile = (int)(y / p->var.tz) * p->tiles_x + tx;
+        yl = y % p->var.tz;
+    }
+    out.tile = tile;
+    out.e.z = (int32_t)z;
+    out.e.yx = (int32_t)((yl << 16) | (x % p->var.tx));
+    out.e.col = col;
+    out.e.scale = scale;
+    return FD_OK;
+}
+
+int build_table(const fd_plan *p, int n, const int64_t *idx, float scale, std::vector<int32_t> &ptr,
+                std::vector<PtEntry> &ent)
+{
+    std::vector<Pt> pts(n);
+    for (int i = 0; i < n; ++i) {
+        int st = locate(p, idx[i], i, scale, pts[i]);
+        if (st) return st;
+    }
+    std::stable_sort(pts.begin(), pts.end(), [](const Pt &a, const Pt &b) {
+        return a.tile != b.tile ? a.tile < b.tile : a.e.z < b.e.z;
+    });
+    ptr.assign(p->ntiles + 1, 0);
+    for (auto &q : pts) ptr[q.tile + 1]++;
+    for (int t = 0; t < p->ntiles; ++t) ptr[t + 1] += ptr[t];
+    ent.resize(pts.size());
+    for (size_t i = 0; i < pts.size(); ++i) ent[i] = pts[i].e;
+    return FD_OK;
+}
+
+int make_tables(const fd_plan *p, int nsrc, const int64_t *src, int nrec, const int64_t *rec,
+                bool adj, Tables &T)
+{
+    const fd_problem &pr = p->prob;
+    const double hd = std::pow(pr.h, pr.dim);
+    const float src_scale = (float)(pr.dt * pr.dt / hd);
+    std::vector<int32_t> a, b, c, d;
+    std::vector<PtEntry> ea, eb, ec, ed;
+    int st;
+    if ((st = build_table(p, nsrc, src, src_scale, a, ea))) return st;
+    if ((st = build_table(p, nrec, rec, 1.0f, b, eb))) return st;
+    if (adj) {
+        // adjoint (q = s2 nu form): residual injected as kappa * h^2 * r (kappa applied
+        // in the kernel); source samples give dJ/ds = q tau^2 / (h^dim h^2 kappa)
+        if ((st = build_table(p, nrec, rec, (float)(pr.h * pr.h), c, ec))) return st;
+        if ((st = build_table(p, nsrc, src, (float)(pr.dt * pr.dt / (hd * pr.h * pr.h)), d, ed))) return st;
+    }
+    const size_t ptrb = up((p->ntiles + 1) * sizeof(int32_t));
+    const size_t sb = up(std::max(nsrc, 1) * sizeof(PtEntry)), rb = up(std::max(nrec, 1) * sizeof(PtEntry));
+    T.blob.assign(table_bytes(p, nsrc, nrec, adj), 0);
+    size_t o = 0;
+    auto put = [&](size_t &off, const void *src_, size_t bytes, size_t span) {
+        off = o;
+        if (bytes) std::memcpy(T.blob.data() + o, src_, bytes);
+        o += span;
+    };
+    put(T.inj_ptr, a.data(), a.size() * 4, ptrb);
+    put(T.inj, ea.data(), ea.size() * sizeof(PtEntry), sb);
+    put(T.smp_ptr, b.data(), b.size() * 4, ptrb);
+    put(T.smp, eb.data(), eb.size() * sizeof(PtEntry), rb);
+    T.has_adj = adj;
+    if (adj) {
+        put(T.ainj_ptr, c.data(), c.size() * 4, ptrb);
+        put(T.ainj, ec.data(), ec.size() * sizeof(PtEntry), rb);
+        put(T.asmp_ptr, d.data(), d.size() * 4, ptrb);
+        put(T.asmp, ed.data(), ed.size() * sizeof(PtEntry), sb);
+    }
+    return FD_OK;
+}
+
+// ------------------------------- tuning -----------------------------------
+
+int ensure_tuned(fd_plan *p)
+{
+    if (p->tuned) return FD_OK;
+    if (p->prob.dim == 3) {
+        int dev = 0, nsm = 152, occ = 1;
+        FDW_CK(cudaGetDevice(&dev));
+        FDW_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        int smem_sm = 0;
+        FDW_CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        occ = std::max(1, std::min((int)(smem_sm / (p->var.smem + 2048)), 2048 / p->var.threads));
+        const int64_t slots = (int64_t)nsm * occ;
+        const int M = p->st.M;
+        double best = 1e300;
+        int bestc = 1;
+        for (int c = 1; c <= 64; ++c) {
+            const int64_t chunk = (p->pad[0] + c - 1) / c;
+            if (c > 1 && chunk < 2 * M) break;
+            const int64_t ctas = (int64_t)p->ntiles * c;
+            const double waves = std::ceil((double)ctas / slots);
+            const double cost = waves * (chunk + 0.5 * 2 * M);
+            if (cost < best * 0.999) { best = cost; bestc = c; }
+        }
+        p->zchunk = (int)((p->pad[0] + bestc - 1) / bestc);
+        p->nz_chunks = (int)((p->pad[0] + p->zchunk - 1) / p->zchunk);
+    }
+    p->tuned = true;
+    return FD_OK;
+}
+
+void fill_params(const fd_plan *p, StepParams &sp)
+{
+    std::memset(&sp, 0, sizeof sp);
+    sp.nz = p->pad[0];
+    sp.ny = p->pad[1];
+    sp.nx = p->pad[2];
+    sp.pitch = p->pitch;
+    sp.plane = p->plane;
+    const fd_problem &pr = p->prob;
+    sp.phys_lo[0] = pr.nb; sp.phys_hi[0] = pr.nb + pr.n[2] - 1;
+    if (pr.dim == 3) { sp.phys_lo[1] = pr.nb; sp.phys_hi[1] = pr.nb + pr.n[1] - 1; }
+    sp.phys_lo[2] = pr.nb; sp.phys_hi[2] = pr.nb + pr.n[0] - 1;
+    sp.gcoef = p->gcoef;
+    sp.tiles_x = p->tiles_x;
+    sp.tiles_y = p->tiles_y;
+    sp.zchunk = p->zchunk;
+    sp.nz_chunks = p->nz_chunks;
+    std::memcpy(sp.w, p->W, sizeof sp.w);
+}
+
+cudaError_t launch(const fd_plan *p, int mode, const StepParams &sp, cudaStream_t s)
+{
+    return p->prob.dim == 2 ? launch_step2d(p->var, mode, sp, s) : launch_step3d(p->var, mode, sp, s);
+}
+
+int encode_field_map(const fd_plan *p, CUtensorMap *map, const float *base)
+{
+    int64_t dims[3], str[2];
+    int box[3];
+    if (p->prob.dim == 2) {
+        dims[0] = p->pad[2]; dims[1] = p->pad[0];
+        str[0] = p->pitch * 4;
+        box[0] = p->var.box[0]; box[1] = p->var.box[1];
+        return encode_tmap(map, base, 2, dims, str, box);
+    }
+    dims[0] = p->pad[2]; dims[1] = p->pad[1]; dims[2] = p->pad[0];
+    str[0] = p->pitch * 4; str[1] = p->plane * 4;
+    box[0] = p->var.box[0]; box[1] = p->var.box[1]; box[2] = 1;
+    return encode_tmap(map, base, 3, dims, str, box);
+}
+
+int check_common(const fd_plan *p, int model_kind, const float *model, int nsrc,
+                 const int64_t *src, const float *wav, int nrec, const int64_t *rec, void *ws,
+                 size_t ws_bytes, size_t need)
+{
+    if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
+    if (model_kind != FD_MODEL_VELOCITY && model_kind != FD_MODEL_SLOWNESS2)
+        return set_error(FD_ERR_ARG, "unknown model kind %d", model_kind);
+    if (!model) return set_error(FD_ERR_ARG, "model is NULL");
+    if (nsrc < 0 || nrec < 0) return set_error(FD_ERR_ARG, "negative source/receiver count");
+    if (nsrc > 0 && (!src || !wav)) return set_error(FD_ERR_ARG, "sources need indices and a wavelet");
+    if (nrec > 0 && !rec) return set_error(FD_ERR_ARG, "receivers need indices");
+    if (!ws) return set_error(FD_ERR_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return set_error(FD_ERR_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < need)
+        return set_error(FD_ERR_NOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+    return FD_OK;
+}
+
+}  // namespace
+}  // namespace fdw
+
+using namespace fdw;
+
+// --------------------------------- ABI ------------------------------------
+
+extern "C" const char *fd_last_error(void) { return g_err; }
+
+extern "C" const char *fd_version(void) { return "fdwave 0.1 (sm_103a)"; }
+
+extern "C" int fd_plan_create(const fd_problem *prob, const fd_stencil_desc *stencil, fd_plan **out)
+{
+    clear_error();
+    if (!prob || !stencil || !out) return set_error(FD_ERR_ARG, "NULL argument to fd_plan_create");
+    *out = nullptr;
+    const fd_problem &pr = *prob;
+    if (pr.dim != 2 && pr.dim != 3) return set_error(FD_ERR_ARG, "dim must be 2 or 3");
+    if (stencil->dim != pr.dim) return set_error(FD_ERR_ARG, "stencil dim %d != problem dim %d", stencil->dim, pr.dim);
+    if (pr.n[0] < 1 || pr.n[2] < 1 || pr.n[1] < 1 || (pr.dim == 2 && pr.n[1] != 1))
+        return set_error(FD_ERR_ARG, "grid sizes must be >= 1 (ny = 1 in 2D)");
+    if (pr.nb < 0 || pr.nt < 0) return set_error(FD_ERR_ARG, "nb and nt must be >= 0");
+    if (!(pr.h > 0) || !(pr.dt > 0) || !(pr.vmax > 0)) return set_error(FD_ERR_ARG, "h, dt and vmax must be > 0");
+    const int64_t padx = pr.n[2] + 2 * pr.nb, pady = pr.dim == 3 ? pr.n[1] + 2 * pr.nb : 1,
+                  padz = pr.n[0] + 2 * pr.nb;
+    if (padx > (1 << 24) || pady > (1 << 24) || padz > (1 << 24) || padx * pady * padz > (int64_t)1 << 36)
+        return set_error(FD_ERR_ARG, "grid too large");
+    if (padx >= 65536 * 64 || (pr.dim == 3 && pady > 32767 * 16))
+        return set_error(FD_ERR_ARG, "grid too large for the tile tables");
+    fd_plan *p = new (std::nothrow) fd_plan();
+    if (!p) return set_error(FD_ERR_NOMEM, "host allocation failed");
+    p->prob = pr;
+    p->st = *stencil;
+    int st = compute_weights(stencil, p->keys, p->mult, p->w, nullptr, nullptr);
+    if (!st) st = compute_cfl(stencil, p->w, &p->cmax);
+    if (st) { delete p; return st; }
+    const double C = pr.vmax * pr.dt / pr.h;
+    if (C > p->cmax * (1.0 + 1e-12)) {
+        delete p;
+        return set_error(FD_ERR_UNSTABLE, "Courant number %.6g exceeds the stability limit %.6g", C, p->cmax);
+    }
+    // weight table W[p][q] and the effective shape (all-zero off-axis orbits -> cross)
+    std::memset(p->W, 0, sizeof p->W);
+    bool offaxis = false;
+    for (size_t k = 0; k < p->keys.size(); ++k) {
+        const int a = p->keys[k][0], b = p->keys[k][1];
+        const float v = (float)p->w[k];
+        p->W[a * kWDim + b] = v;
+        p->W[b * kWDim + a] = v;
+        if (b != 0 && p->w[k] != 0.0) offaxis = true;
+    }
+    p->shape_eff = offaxis ? stencil->shape : FD_CROSS;
+    p->pad[0] = padz; p->pad[1] = pady; p->pad[2] = padx;
+    p->pitch = (padx + 31) / 32 * 32;
+    p->plane = pr.dim == 3 ? p->pitch * pady : p->pitch * padz;
+    p->field = pr.dim == 3 ? p->plane * padz : p->plane;
+    p->field = (p->field + 63) / 64 * 64;
+    const int M = stencil->M;
+    if (pr.dim == 2) {
+        st = select_variant_2d(p->shape_eff, M, stencil->N, padx, padz, &p->var);
+        p->tiles_x = (int)((padx + p->var.tx - 1) / p->var.tx);
+        p->tiles_y = (int)((padz + p->var.tz - 1) / p->var.tz);
+    } else {
+        if (p->shape_eff == FD_CROSS_RHOMBUS || p->shape_eff == FD_CROSS_SQUARE || M > 8) {
+            delete p;
+            return set_error(FD_ERR_UNSUPPORTED, "3D kernels support cross, rhombus and square shapes with M <= 8");
+        }
+        st = select_variant_3d(p->shape_eff, M, stencil->N, padx, pady, padz, &p->var);
+        p->tiles_x = (int)((padx + p->var.tx - 1) / p->var.tx);
+        p->tiles_y = (int)((pady + p->var.tz - 1) / p->var.tz);
+        p->zchunk = (int)padz;
+        p->nz_chunks = 1;
+    }
+    if (st) {
+        delete p;
+        return set_error(FD_ERR_UNSUPPORTED, "no kernel for shape %d, M %d in %dD", p->shape_eff, M, pr.dim);
+    }
+    p->ntiles = p->tiles_x * p->tiles_y;
+    if (pr.nb > 0) {
+        const double R = pr.damp_R > 0 ? pr.damp_R : 1e-3;
+        const double eta_max = 3.0 * pr.vmax * std::log(1.0 / R) / (2.0 * pr.nb * pr.h);
+        p->gcoef = (float)(0.5 * pr.dt * eta_max / ((double)pr.nb * pr.nb));
+    }
+    *out = p;
+    return FD_OK;
+}
+
+extern "C" void fd_plan_destroy(fd_plan *plan) { delete plan; }
+
+extern "C" int fd_plan_get_info(const fd_plan *p, fd_plan_info *info)
+{
+    clear_error();
+    if (!p || !info) return set_error(FD_ERR_ARG, "NULL argument");
+    for (int i = 0; i < 3; ++i) info->padded[i] = p->pad[i];
+    info->pitch = p->pitch;
+    info->n_orbits = (int)p->keys.size();
+    info->kernel = (p->prob.dim * 100 + p->var.shape * 10) + (p->var.generic ? 1 : 0);
+    info->courant_max = p->cmax;
+    info->tile[0] = p->var.tx;
+    info->tile[1] = p->var.tz;
+    info->tile[2] = p->zchunk;
+    info->effective_shape = p->shape_eff;
+    return FD_OK;
+}
+
+extern "C" int fd_forward_workspace_size(const fd_plan *p, int nsrc, int nrec, size_t *bytes)
+{
+    clear_error();
+    if (!p || !bytes || nsrc < 0 || nrec < 0) return set_error(FD_ERR_ARG, "bad argument");
+    *bytes = make_layout(p, nsrc, nrec, false, 1).total;
+    return FD_OK;
+}
+
+extern "C" int fd_gradient_workspace_size(const fd_plan *p, int nsrc, int nrec, int k, size_t *bytes)
+{
+    clear_error();
+    if (!p || !bytes || nsrc < 0 || nrec < 0 || k < 1) return set_error(FD_ERR_ARG, "bad argument");
+    *bytes = make_layout(p, nsrc, nrec, true, std::min(k, std::max(p->prob.nt, 1))).total;
+    return FD_OK;
+}
+
+namespace {
+
+int upload_tables(fd_plan *p, const Layout &L, char *ws, const Tables &T, cudaStream_t s)
+{
+    FDW_CK(cudaMemcpyAsync(ws + L.tab, T.blob.data(), T.blob.size(), cudaMemcpyHostToDevice, s));
+    return FD_OK;
+}
+
+int upload_maps(fd_plan *p, const Layout &L, char *ws, int nbuf, cudaStream_t s)
+{
+    std::vector<CUtensorMap> maps(nbuf);
+    for (int i = 0; i < nbuf; ++i) {
+        int r = encode_field_map(p, &maps[i], reinterpret_cast<const float *>(ws + L.buf[i]));
+        if (r) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", r);
+    }
+    FDW_CK(cudaMemcpyAsync(ws + L.tmaps, maps.data(), nbuf * sizeof(CUtensorMap),
+                           cudaMemcpyHostToDevice, s));
+    return FD_OK;
+}
+
+// stride between consecutive z (rows in 2D, planes in 3D), in floats
+int64_t zstride(const fd_plan *p) { return p->prob.dim == 3 ? p->plane : p->pitch; }
+
+int prep_model(fd_plan *p, const Layout &L, char *ws, int kind, const float *model, cudaStream_t s)
+{
+    const fd_problem &pr = p->prob;
+    const int64_t phys[3] = {pr.n[0], pr.n[1], pr.n[2]};
+    const float vmax2 = (float)(pr.vmax * pr.vmax * (1.0 + 1e-6));
+    FDW_CK(launch_prep_kappa(model, kind, reinterpret_cast<float *>(ws + L.kappa), pr.dim, phys,
+                             pr.nb, p->pad, p->pitch, zstride(p), pr.dt / pr.h, vmax2,
+                             reinterpret_cast<int *>(ws + L.status), s));
+    return FD_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Copy a packed padded state [2][pad] into / out of two pitched buffers.
+int state_in(fd_plan *p, const float *src, float *b0, float *b1, cudaStream_t s)
+{
+    const int64_t n = p->pad[0] * p->pad[1] * p->pad[2];
+    FDW_CK(launch_copy_state(src, p->pad[2], p->pad[2] * p->pad[1], b0, p->pitch, zstride(p), p->pad, s));
+    FDW_CK(launch_copy_state(src + n, p->pad[2], p->pad[2] * p->pad[1], b1, p->pitch, zstride(p), p->pad, s));
+    return FD_OK;
+}
+
+int state_out(fd_plan *p, const float *b0, const float *b1, float *dst, cudaStream_t s)
+{
+    const int64_t n = p->pad[0] * p->pad[1] * p->pad[2];
+    FDW_CK(launch_copy_state(b0, p->pitch, zstride(p), dst, p->pad[2], p->pad[2] * p->pad[1], p->pad, s));
+    FDW_CK(launch_copy_state(b1, p->pitch, zstride(p), dst + n, p->pad[2], p->pad[2] * p->pad[1], p->pad, s));
+    return FD_OK;
+}
+
+struct FwdBind {
+    const PtEntry *inj, *smp;
+    const int32_t *inj_ptr, *smp_ptr;
+};
+
+}  // namespace
+
+extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int nsrc,
+                          const int64_t *src, const float *wavelet, int nrec, const int64_t *rec,
+                          float *traces, const float *state_in_d, float *state_out_d, void *ws,
+                          size_t ws_bytes, void *stream)
+{
+    clear_error();
+    if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
+    const Layout L = make_layout(p, nsrc, nrec, false, 1);
+    int st = check_common(p, model_kind, model, nsrc, src, wavelet, nrec, rec, ws, ws_bytes, L.total);
+    if (st) return st;
+    if (nrec > 0 && !traces) return set_error(FD_ERR_ARG, "traces is NULL");
+    if ((st = ensure_tuned(p))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *w = reinterpret_cast<char *>(ws);
+    Tables T;
+    if ((st = make_tables(p, nsrc, src, nrec, rec, false, T))) return st;
+    if ((st = upload_tables(p, L, w, T, s))) return st;
+    if ((st = upload_maps(p, L, w, 2, s))) return st;
+    FDW_CK(cudaMemsetAsync(w + L.status, 0, kAlign, s));
+    float *A = reinterpret_cast<float *>(w + L.buf[0]);
+    float *B = reinterpret_cast<float *>(w + L.buf[1]);
+    const size_t fb = (size_t)p->field * sizeof(float);
+    FDW_CK(cudaMemsetAsync(A, 0, fb, s));
+    FDW_CK(cudaMemsetAsync(B, 0, fb, s));
+    if ((st = prep_model(p, L, w, model_kind, model, s))) return st;
+    if (state_in_d && (st = state_in(p, state_in_d, A, B, s))) return st;
+    const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(w + L.tmaps);
+    StepParams sp;
+    fill_params(p, sp);
+    sp.kappa = reinterpret_cast<const float *>(w + L.kappa);
+    sp.status = reinterpret_cast<int *>(w + L.status);
+    if (nsrc > 0) {
+        sp.inj_ptr = reinterpret_cast<const int32_t *>(w + L.tab + T.inj_ptr);
+        sp.inj = reinterpret_cast<const PtEntry *>(w + L.tab + T.inj);
+        sp.inj_series = wavelet;
+        sp.inj_ncol = nsrc;
+    }
+    if (nrec > 0) {
+        sp.smp_ptr = reinterpret_cast<const int32_t *>(w + L.tab + T.smp_ptr);
+        sp.smp = reinterpret_cast<const PtEntry *>(w + L.tab + T.smp);
+        sp.smp_out = traces;
+        sp.smp_ncol = nrec;
+    }
+    for (int n = 0; n < p->prob.nt; ++n) {
+        const int cur = n & 1;
+        sp.tmap = maps + cur;
+        sp.u_prev = cur ? A : B;
+        sp.step = n;
+        FDW_CK(launch(p, kModeForward, sp, s));
+    }
+    if (state_out_d) {
+        const bool even = (p->prob.nt % 2) == 0;
+        if ((st = state_out(p, even ? A : B, even ? B : A, state_out_d, s))) return st;
+    }
+    p->last_ws = ws;
+    return FD_OK;
+}
+
+extern "C" int fd_status_read(const fd_plan *p, void *ws, void *stream)
+{
+    clear_error();
+    if (!p || !ws) return set_error(FD_ERR_ARG, "NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int word = 0;
+    FDW_CK(cudaMemcpyAsync(&word, ws, sizeof word, cudaMemcpyDeviceToHost, s));
+    FDW_CK(cudaStreamSynchronize(s));
+    FDW_CK(cudaMemsetAsync(ws, 0, sizeof word, s));
+    if (word & kStatusTimeout) return set_error(FD_ERR_TIMEOUT, "a bounded device wait timed out");
+    if (word & kStatusVmax) return set_error(FD_ERR_UNSTABLE, "model velocity exceeds the plan's vmax");
+    return FD_OK;
+}
+
+extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *model, int nsrc,
+                                   const int64_t *src, const float *wavelet, int nrec,
+                                   const int64_t *rec, const float *resid, int k, float *grad,
+                                   float *traces, float *wavelet_grad, void *ws, size_t ws_bytes,
+                                   void *stream)
+{
+    clear_error();
+    if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
+    if (k < 1) return set_error(FD_ERR_ARG, "ckpt_every must be >= 1");
+    const int nt = p->prob.nt;
+    k = std::min(k, std::max(nt, 1));
+    const Layout L = make_layout(p, nsrc, nrec, true, k);
+    int st = check_common(p, model_kind, model, nsrc, src, wavelet, nrec, rec, ws, ws_bytes, L.total);
+    if (st) return st;
+    if (!grad) return set_error(FD_ERR_ARG, "grad is NULL");
+    if (nrec > 0 && !resid) return set_error(FD_ERR_ARG, "resid is NULL");
+    if ((st = ensure_tuned(p))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *w = reinterpret_cast<char *>(ws);
+    Tables T;
+    if ((st = make_tables(p, nsrc, src, nrec, rec, true, T))) return st;
+    if ((st = upload_tables(p, L, w, T, s))) return st;
+    if ((st = upload_maps(p, L, w, 4, s))) return st;
+    FDW_CK(cudaMemsetAsync(w + L.status, 0, kAlign, s));
+    const size_t fb = up((size_t)p->field * sizeof(float));
+    float *buf[4];
+    for (int i = 0; i < 4; ++i) {
+        buf[i] = reinterpret_cast<float *>(w + L.buf[i]);
+        FDW_CK(cudaMemsetAsync(buf[i], 0, fb, s));
+    }
+    float *gacc = reinterpret_cast<float *>(w + L.gacc);
+    FDW_CK(cudaMemsetAsync(gacc, 0, fb, s));
+    if ((st = prep_model(p, L, w, model_kind, model, s))) return st;
+    const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(w + L.tmaps);
+    char *ck = w + L.ckpt;
+    char *dseg = w + L.dseg;
+
+    StepParams sp;
+    fill_params(p, sp);
+    sp.kappa = reinterpret_cast<const float *>(w + L.kappa);
+    sp.status = reinterpret_cast<int *>(w + L.status);
+    auto bind_fwd = [&](bool sample) {
+        sp.inj_ptr = nsrc ? reinterpret_cast<const int32_t *>(w + L.tab + T.inj_ptr) : nullptr;
+        sp.inj = reinterpret_cast<const PtEntry *>(w + L.tab + T.inj);
+        sp.inj_series = wavelet;
+        sp.inj_ncol = nsrc;
+        sp.smp_ptr = (sample && nrec && traces) ? reinterpret_cast<const int32_t *>(w + L.tab + T.smp_ptr) : nullptr;
+        sp.smp = reinterpret_cast<const PtEntry *>(w + L.tab + T.smp);
+        sp.smp_out = traces;
+        sp.smp_ncol = nrec;
+    };
+    // forward sweep with checkpoints (u^n, u^{n-1}) at n = s k
+    bind_fwd(true);
+    for (int n = 0; n < nt; ++n) {
+        const int cur = n & 1;
+        if (n % k == 0) {
+            const int c = n / k;
+            FDW_CK(cudaMemcpyAsync(ck + (size_t)(2 * c) * fb, buf[cur], fb, cudaMemcpyDeviceToDevice, s));
+            FDW_CK(cudaMemcpyAsync(ck + (size_t)(2 * c + 1) * fb, buf[cur ^ 1], fb, cudaMemcpyDeviceToDevice, s));
+        }
+        sp.tmap = maps + cur;
+        sp.u_prev = buf[cur ^ 1];
+        sp.step = n;
+        FDW_CK(launch(p, kModeForward, sp, s));
+    }
+    // backward sweep over segments
+    int t = 0;   // adjoint steps done: q^{j+1} lives in buf[2 + (t & 1)]
+    for (int c = L.nck - 1; c >= 0; --c) {
+        const int k0 = c * k, k1 = std::min(k0 + k, nt);
+        FDW_CK(cudaMemcpyAsync(buf[0], ck + (size_t)(2 * c) * fb, fb, cudaMemcpyDeviceToDevice, s));
+        FDW_CK(cudaMemcpyAsync(buf[1], ck + (size_t)(2 * c + 1) * fb, fb, cudaMemcpyDeviceToDevice, s));
+        bind_fwd(false);
+        for (int n = k0; n < k1; ++n) {
+            const int cur = (n - k0) & 1;
+            sp.tmap = maps + cur;
+            sp.u_prev = buf[cur ^ 1];
+            sp.step = n;
+            sp.dseg_out = reinterpret_cast<float *>(dseg + (size_t)(n - k0) * fb);
+            FDW_CK(launch(p, kModeStoreD, sp, s));
+        }
+        sp.dseg_out = nullptr;
+        sp.inj_ptr = nrec ? reinterpret_cast<const int32_t *>(w + L.tab + T.ainj_ptr) : nullptr;
+        sp.inj = reinterpret_cast<const PtEntry *>(w + L.tab + T.ainj);
+        sp.inj_series = resid;
+        sp.inj_ncol = nrec;
+        sp.smp_ptr = (nsrc && wavelet_grad) ? reinterpret_cast<const int32_t *>(w + L.tab + T.asmp_ptr) : nullptr;
+        sp.smp = reinterpret_cast<const PtEntry *>(w + L.tab + T.asmp);
+        sp.smp_out = wavelet_grad;
+        sp.smp_ncol = nsrc;
+        sp.gacc = gacc;
+        for (int j = k1; j > k0; --j, ++t) {
+            const int cur = 2 + (t & 1);
+            sp.tmap = maps + cur;
+            sp.u_prev = buf[cur ^ 1];
+            sp.step = j - 1;
+            sp.dseg_in = reinterpret_cast<const float *>(dseg + (size_t)(j - 1 - k0) * fb);
+            FDW_CK(launch(p, kModeAdjoint, sp, s));
+        }
+        sp.gacc = nullptr;
+        sp.dseg_in = nullptr;
+    }
+    const fd_problem &pr = p->prob;
+    const int64_t phys[3] = {pr.n[0], pr.n[1], pr.n[2]};
+    FDW_CK(launch_fold_grad(gacc, p->pitch, zstride(p), phys, pr.nb, (float)(-1.0 / (pr.dt * pr.dt)),
+                            grad, s));
+    p->last_ws = ws;
+    return FD_OK;
+}
+
+// ------------------------------ batched shots ------------------------------
+// Each shot gets its own slice of the workspace (forward layout); every time
+// step launches the step kernel of each shot in turn, and the whole time loop
+// is captured once into a CUDA graph and replayed.
+
+extern "C" int fd_forward_batched_workspace_size(int nshots, const fd_shot *shots, size_t *bytes)
+{
+    clear_error();
+    if (nshots < 0 || (nshots > 0 && !shots) || !bytes) return set_error(FD_ERR_ARG, "bad argument");
+    size_t tot = 0;
+    for (int i = 0; i < nshots; ++i) {
+        if (!shots[i].plan) return set_error(FD_ERR_ARG, "shot %d has no plan", i);
+        tot += make_layout(shots[i].plan, shots[i].nsrc, shots[i].nrec, false, 1).total;
+    }
+    *bytes = tot;
+    return FD_OK;
+}
+
+extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, size_t ws_bytes,
+                                  void *stream)
+{
+    clear_error();
+    size_t need = 0;
+    int st = fd_forward_batched_workspace_size(nshots, shots, &need);
+    if (st) return st;
+    if (!ws || ws_bytes < need) return set_error(FD_ERR_NOMEM, "workspace too small (%zu < %zu)", ws_bytes, need);
+    if (nshots == 0) return FD_OK;
+    const fd_plan *p0 = shots[0].plan;
+    for (int i = 1; i < nshots; ++i) {
+        const fd_plan *q = shots[i].plan;
+        if (q->prob.dim != p0->prob.dim || q->prob.nt != p0->prob.nt || q->prob.dt != p0->prob.dt ||
+            q->st.M != p0->st.M || q->st.shape != p0->st.shape || q->st.scheme != p0->st.scheme)
+            return set_error(FD_ERR_ARG, "shot %d: batched shots must share dim, stencil, dt and nt", i);
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *base = reinterpret_cast<char *>(ws);
+    std::vector<StepParams> sps(nshots);
+    std::vector<float *> As(nshots), Bs(nshots);
+    std::vector<const CUtensorMap *> mp(nshots);
+    for (int i = 0; i < nshots; ++i) {
+        fd_plan *p = const_cast<fd_plan *>(shots[i].plan);
+        const fd_shot &sh = shots[i];
+        const Layout L = make_layout(p, sh.nsrc, sh.nrec, false, 1);
+        st = check_common(p, sh.model_kind, sh.model_d, sh.nsrc, sh.src_idx, sh.wavelet_d, sh.nrec,
+                          sh.rec_idx, base, L.total, L.total);
+        if (st) return set_error(st, "shot %d: %s", i, fd_last_error());
+        if ((st = ensure_tuned(p))) return st;
+        Tables T;
+        if ((st = make_tables(p, sh.nsrc, sh.src_idx, sh.nrec, sh.rec_idx, false, T))) return st;
+        if ((st = upload_tables(p, L, base, T, s))) return st;
+        if ((st = upload_maps(p, L, base, 2, s))) return st;
+        FDW_CK(cudaMemsetAsync(base + L.status, 0, kAlign, s));
+        As[i] = reinterpret_cast<float *>(base + L.buf[0]);
+        Bs[i] = reinterpret_cast<float *>(base + L.buf[1]);
+        FDW_CK(cudaMemsetAsync(As[i], 0, (size_t)p->field * 4, s));
+        FDW_CK(cudaMemsetAsync(Bs[i], 0, (size_t)p->field * 4, s));
+        if ((st = prep_model(p, L, base, sh.model_kind, sh.model_d, s))) return st;
+        StepParams &sp = sps[i];
+        fill_params(p, sp);
+        sp.kappa = reinterpret_cast<const float *>(base + L.kappa);
+        sp.status = reinterpret_cast<int *>(base + L.status);
+        if (sh.nsrc > 0) {
+            sp.inj_ptr = reinterpret_cast<const int32_t *>(base + L.tab + T.inj_ptr);
+            sp.inj = reinterpret_cast<const PtEntry *>(base + L.tab + T.inj);
+            sp.inj_series = sh.wavelet_d;
+            sp.inj_ncol = sh.nsrc;
+        }
+        if (sh.nrec > 0) {
+            sp.smp_ptr = reinterpret_cast<const int32_t *>(base + L.tab + T.smp_ptr);
+            sp.smp = reinterpret_cast<const PtEntry *>(base + L.tab + T.smp);
+            sp.smp_out = sh.traces_d;
+            sp.smp_ncol = sh.nrec;
+        }
+        mp[i] = reinterpret_cast<const CUtensorMap *>(base + L.tmaps);
+        base += L.total;
+    }
+    // capture the time loop into a graph (a side stream is used for capture so
+    // that the caller's stream may be the legacy default stream)
+    cudaStream_t cs;
+    FDW_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t ev;
+    FDW_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    FDW_CK(cudaEventRecord(ev, s));
+    FDW_CK(cudaStreamWaitEvent(cs, ev, 0));
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    FDW_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaSuccess;
+    const int nt = p0->prob.nt;
+    for (int n = 0; n < nt && ce == cudaSuccess; ++n)
+        for (int i = 0; i < nshots && ce == cudaSuccess; ++i) {
+            StepParams &sp = sps[i];
+            const int cur = n & 1;
+            sp.tmap = mp[i] + cur;
+            sp.u_prev = cur ? As[i] : Bs[i];
+            sp.step = n;
+            ce = launch(shots[i].plan, kModeForward, sp, cs);
+        }
+    cudaError_t ee = cudaStreamEndCapture(cs, &g);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        cudaEventDestroy(ev);
+        return set_error(FD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    FDW_CK(cudaGraphInstantiate(&ge, g, 0));
+    FDW_CK(cudaGraphLaunch(ge, cs));
+    FDW_CK(cudaEventRecord(ev, cs));
+    FDW_CK(cudaStreamWaitEvent(s, ev, 0));
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaEventDestroy(ev);
+    return FD_OK;
+}

@@ -1,0 +1,337 @@
+// 2D leapfrog step with a shaped stencil (paper Eq. spacexz_derivative2_sym,
+// Eq. time_derivative1, damping term of Section 3.1), fused with point-source
+// injection, receiver sampling and the FWI modes (store D / adjoint with
+// gradient accumulation).
+//
+// One CTA computes a tile of 64 columns x (16 R) rows.  The tile plus its halo
+// (HX = round4(M) columns, M rows on each side) is brought into shared memory
+// by one TMA load whose out-of-bounds elements are zero-filled: that is the
+// zero field outside the padded grid.  Thread (tx, ty) owns 4 consecutive
+// columns (one float4) of R consecutive rows.
+#include "device_common.cuh"
+
+namespace fdw {
+
+namespace {
+
+constexpr int kTX = 64;     // output columns per tile
+constexpr int kTZ = 16;     // thread rows per tile
+constexpr int kThreads = 256;
+
+// Visit the tile's table entries owned by this thread: f(r, j, entry).
+template <int R, class F>
+__device__ __forceinline__ void for_owned(const int32_t *ptr, const PtEntry *tab, int tile,
+                                          int z0, int tx, int ty, F f)
+{
+    const int b = ptr[tile], e = ptr[tile + 1];
+    for (int k = b; k < e; ++k) {
+        const PtEntry en = tab[k];
+        const int zl = en.z - z0 - ty * R;
+        const int xl = en.yx & 0xffff;
+        if (zl >= 0 && zl < R && (xl >> 2) == tx) f(zl, xl & 3, en);
+    }
+}
+
+template <int SHAPE, int M, int NN, int MODE, int R>
+__global__ void __launch_bounds__(kThreads) step2d_kernel(const __grid_constant__ StepParams p)
+{
+    constexpr int HX = round4(M);
+    constexpr int SW = kTX + 2 * HX;
+    constexpr int SH = kTZ * R + 2 * M;
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t bar;
+
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % p.tiles_x) * kTX;
+    const int z0 = (tile / p.tiles_x) * (kTZ * R);
+
+    if (threadIdx.x == 0) {
+        prefetch_tmap(p.tmap);
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, SW * SH * 4);
+        tma_load_2d(sm, p.tmap, &bar, x0 - HX, z0 - M);
+    }
+
+    const int xg = x0 + 4 * tx;
+    const bool colok = xg < p.nx;
+    float4 up[R], kp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int zg = z0 + ty * R + r;
+        if (colok && zg < p.nz) {
+            const int64_t o = (int64_t)zg * p.pitch + xg;
+            up[r] = ldg4(p.u_prev + o);
+            kp[r] = ldg4(p.kappa + o);
+        } else {
+            up[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            kp[r] = up[r];
+        }
+    }
+    float d2x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d2x[j] = layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]);
+
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(p.status, kStatusTimeout);
+            mbar_wait_bounded(&bar, 0);   // let an in-flight copy land before exiting
+        }
+        return;
+    }
+
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const int zl = M + ty * R + r;
+        const int zg = z0 + ty * R + r;
+        float lap[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q <= M; ++q) {
+            const int E = shape_ext(SHAPE, M, NN, q);
+            if (E < 0) continue;
+            const int E4 = round4(E);
+            float win[4 + 2 * round4(M)];
+            const float *rp = sm + (zl + q) * SW + HX + 4 * tx - E4;
+            const float *rm = sm + (zl - q) * SW + HX + 4 * tx - E4;
+#pragma unroll
+            for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
+                float4 a = ld4(rp + 4 * i);
+                if (q > 0) {
+                    const float4 b = ld4(rm + 4 * i);
+                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                }
+                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float acc = p.w[q] * win[E4 + j];   // W[0][q]
+#pragma unroll
+                for (int pp = 1; pp <= E; ++pp)
+                    acc = fmaf(p.w[pp * kWDim + q], win[E4 + j + pp] + win[E4 + j - pp], acc);
+                lap[j] += acc;
+            }
+        }
+        const float4 c = ld4(sm + zl * SW + HX + 4 * tx);
+        const float d2z = layer_d2(zg, p.phys_lo[2], p.phys_hi[2]);
+        const float cc[4] = {c.x, c.y, c.z, c.w};
+        const float uu[4] = {up[r].x, up[r].y, up[r].z, up[r].w};
+        const float kk[4] = {kp[r].x, kp[r].y, kp[r].z, kp[r].w};
+        float o[4], dv[4], g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            g[j] = p.gcoef * (d2x[j] + d2z);
+            dv[j] = kk[j] * lap[j];
+            // (u - u_prev) + u + kappa lap, with (1 - g) u_prev for the sponge
+            o[j] = (cc[j] - uu[j]) + cc[j] + dv[j] + g[j] * uu[j];
+        }
+        // injection inside the bracket; adjoint residuals are scaled by kappa
+        if (p.inj_ptr)
+            for_owned<1>(p.inj_ptr, p.inj, tile, z0 + ty * R + r, tx, 0, [&](int, int j, const PtEntry &en) {
+                float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
+                if (MODE == kModeAdjoint) a *= kk[j];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj == j) o[jj] += a;
+            });
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+        if (p.smp_ptr)
+            for_owned<1>(p.smp_ptr, p.smp, tile, z0 + ty * R + r, tx, 0, [&](int, int j, const PtEntry &en) {
+                float v = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj == j) v = o[jj];
+                v *= en.scale;
+                if (MODE == kModeAdjoint) v /= kk[j];
+                p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
+            });
+        if (!colok || zg >= p.nz) continue;
+        const int64_t off = (int64_t)zg * p.pitch + xg;
+        const float4 un = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4 *>(p.u_prev + off) = un;
+        if (MODE == kModeStoreD)
+            *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+        if (MODE == kModeAdjoint) {
+            const float4 d = ldg4(p.dseg_in + off);
+            float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
+            ga.x = fmaf(un.x, d.x, ga.x); ga.y = fmaf(un.y, d.y, ga.y);
+            ga.z = fmaf(un.z, d.z, ga.z); ga.w = fmaf(un.w, d.w, ga.w);
+            *reinterpret_cast<float4 *>(p.gacc + off) = ga;
+        }
+    }
+}
+
+// Generic runtime-shape 2D kernel (any shape, 1 <= M <= kMaxM): scalar
+// shared-memory reads, one row per thread (R = 1).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant__ StepParams p,
+                                                           int shape, int M, int N)
+{
+    const int HX = round4(M);
+    const int SW = kTX + 2 * HX;
+    const int SH = kTZ + 2 * M;
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t bar;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % p.tiles_x) * kTX;
+    const int z0 = (tile / p.tiles_x) * kTZ;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, SW * SH * 4);
+        tma_load_2d(sm, p.tmap, &bar, x0 - HX, z0 - M);
+    }
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(p.status, kStatusTimeout);
+            mbar_wait_bounded(&bar, 0);
+        }
+        return;
+    }
+    const int xg = x0 + 4 * tx, zg = z0 + ty;
+    const bool live = xg < p.nx && zg < p.nz;
+    const int zl = M + ty;
+    float o[4], dv[4], kk[4], uu[4], gm[4];
+    const int64_t off = (int64_t)zg * p.pitch + xg;
+    const float4 up = live ? ldg4(p.u_prev + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 kp = live ? ldg4(p.kappa + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+    uu[0] = up.x; uu[1] = up.y; uu[2] = up.z; uu[3] = up.w;
+    kk[0] = kp.x; kk[1] = kp.y; kk[2] = kp.z; kk[3] = kp.w;
+    const float d2z = layer_d2(zg, p.phys_lo[2], p.phys_hi[2]);
+    for (int j = 0; j < 4; ++j) {
+        const int xc = HX + 4 * tx + j;
+        float lap = 0.f;
+        for (int q = 0; q <= M; ++q) {
+            const int E = shape_ext(shape, M, N, q);
+            if (E < 0) continue;
+            const float *rp = sm + (zl + q) * SW + xc;
+            const float *rm = sm + (zl - q) * SW + xc;
+            float acc = p.w[q] * (q ? rp[0] + rm[0] : rp[0]);
+            for (int pp = 1; pp <= E; ++pp) {
+                float s = rp[pp] + rp[-pp];
+                if (q) s += rm[pp] + rm[-pp];
+                acc = fmaf(p.w[pp * kWDim + q], s, acc);
+            }
+            lap += acc;
+        }
+        const float c = sm[zl * SW + xc];
+        gm[j] = p.gcoef * (layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2z);
+        dv[j] = kk[j] * lap;
+        o[j] = (c - uu[j]) + c + dv[j] + gm[j] * uu[j];
+    }
+    float4 br = make_float4(o[0], o[1], o[2], o[3]);
+    if (p.inj_ptr)
+        for_owned<1>(p.inj_ptr, p.inj, tile, z0, tx, ty, [&](int r, int j, const PtEntry &en) {
+            float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
+            if (MODE == kModeAdjoint) a *= kk[j];
+            add4(br, j, a);
+        });
+    o[0] = br.x; o[1] = br.y; o[2] = br.z; o[3] = br.w;
+    for (int j = 0; j < 4; ++j)
+        if (gm[j] != 0.f) o[j] = __fdividef(o[j], 1.f + gm[j]);
+    const float4 un = make_float4(o[0], o[1], o[2], o[3]);
+    if (p.smp_ptr)
+        for_owned<1>(p.smp_ptr, p.smp, tile, z0, tx, ty, [&](int r, int j, const PtEntry &en) {
+            float v = get4(un, j) * en.scale;
+            if (MODE == kModeAdjoint) v /= kk[j];
+            p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
+        });
+    if (!live) return;
+    *reinterpret_cast<float4 *>(p.u_prev + off) = un;
+    if (MODE == kModeStoreD)
+        *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+    if (MODE == kModeAdjoint) {
+        const float4 d = ldg4(p.dseg_in + off);
+        float4 g = *reinterpret_cast<float4 *>(p.gacc + off);
+        g.x = fmaf(un.x, d.x, g.x); g.y = fmaf(un.y, d.y, g.y);
+        g.z = fmaf(un.z, d.z, g.z); g.w = fmaf(un.w, d.w, g.w);
+        *reinterpret_cast<float4 *>(p.gacc + off) = g;
+    }
+}
+
+using KernelFn = void (*)(const StepParams);
+
+template <int SHAPE, int M, int R>
+KernelFn pick_mode(int mode)
+{
+    switch (mode) {
+    case kModeForward: return step2d_kernel<SHAPE, M, 0, kModeForward, R>;
+    case kModeStoreD: return step2d_kernel<SHAPE, M, 0, kModeStoreD, R>;
+    default: return step2d_kernel<SHAPE, M, 0, kModeAdjoint, R>;
+    }
+}
+
+// Specialised (shape, M, R) triples; everything else runs the generic kernel.
+KernelFn lookup_fast(int shape, int M, int R, int mode)
+{
+#define FDW_C(S, MM, RR) \
+    if (shape == S && M == MM && R == RR) return pick_mode<S, MM, RR>(mode);
+    FDW_C(FD_CROSS, 2, 1) FDW_C(FD_CROSS, 4, 1) FDW_C(FD_CROSS, 8, 1)
+    FDW_C(FD_CROSS, 2, 4) FDW_C(FD_CROSS, 4, 4) FDW_C(FD_CROSS, 8, 4)
+    FDW_C(FD_RHOMBUS, 2, 4) FDW_C(FD_RHOMBUS, 4, 4) FDW_C(FD_RHOMBUS, 8, 4)
+    FDW_C(FD_SQUARE, 2, 4) FDW_C(FD_SQUARE, 4, 4) FDW_C(FD_SQUARE, 8, 4)
+#undef FDW_C
+    return nullptr;
+}
+
+}  // namespace
+
+int select_variant_2d(int shape, int M, int N, int64_t nx, int64_t nz, Variant *v)
+{
+    v->dim = 2;
+    v->shape = shape;
+    v->M = M;
+    v->N = N;
+    v->threads = kThreads;
+    v->tx = kTX;
+    // R = 4 rows per thread when the grid has enough tiles to fill the GPU
+    // (two CTAs per SM on 152 SMs), else one row per thread.
+    const int64_t tiles4 = ((nx + kTX - 1) / kTX) * ((nz + 4 * kTZ - 1) / (4 * kTZ));
+    int R = tiles4 >= 2 * 152 ? 4 : 1;
+    if (!lookup_fast(shape, M, R, 0)) R = 5 - R;
+    v->generic = lookup_fast(shape, M, R, 0) ? 0 : 1;
+    if (v->generic) R = 1;
+    v->tz = kTZ * R;
+    const int HX = round4(M);
+    v->box[0] = kTX + 2 * HX;
+    v->box[1] = kTZ * R + 2 * M;
+    v->box[2] = 1;
+    v->smem = (size_t)v->box[0] * v->box[1] * sizeof(float);
+    return 0;
+}
+
+cudaError_t launch_step2d(const Variant &v, int mode, const StepParams &p, cudaStream_t s)
+{
+    const int ntiles = p.tiles_x * p.tiles_y;
+    if (ntiles <= 0) return cudaSuccess;
+    if (!v.generic) {
+        KernelFn fn = lookup_fast(v.shape, v.M, v.tz / kTZ, mode);
+        if (!fn) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)v.smem);
+        if (e != cudaSuccess) return e;
+        fn<<<ntiles, kThreads, v.smem, s>>>(p);
+        return cudaGetLastError();
+    }
+    void (*fn)(const StepParams, int, int, int) =
+        mode == kModeForward ? step2d_generic<kModeForward>
+        : mode == kModeStoreD ? step2d_generic<kModeStoreD> : step2d_generic<kModeAdjoint>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)v.smem);
+    if (e != cudaSuccess) return e;
+    fn<<<ntiles, kThreads, v.smem, s>>>(p, v.shape, v.M, v.N);
+    return cudaGetLastError();
+}
+
+}  // namespace fdw

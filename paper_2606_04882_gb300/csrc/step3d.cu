@@ -1,0 +1,296 @@
+// 3D leapfrog step with a shaped stencil (3D extension of Eq.
+// spacexz_derivative2_sym as the union of the 2D shape in the three coordinate
+// planes), fused with damping, injection, sampling and the FWI modes.
+//
+// A CTA owns a 64 x TY column of (x, y) and marches a chunk of z planes.  The
+// planes z-M .. z+M (plus prefetch) of the input field, each with an x halo
+// of round4(M) and a y halo of M, sit in a ring of shared-memory slots filled
+// by TMA (out-of-bounds zero fill = zero field outside the padded grid), one
+// mbarrier per slot.  Thread (tx, ty) owns 4 consecutive x (one float4) of
+// row y0 + ty in every plane of the chunk.
+#include "device_common.cuh"
+
+namespace fdw {
+
+namespace {
+
+constexpr int kTX3 = 64;
+constexpr int kPF = 2;     // planes prefetched beyond the stencil's reach
+
+template <int M>
+constexpr int ring_slots() { return 2 * M + 1 + kPF; }
+
+// Tile table walk for one plane: apply f(j, entry) to owned entries with
+// entry.z == z; `k` advances past them (entries are z-sorted per tile).
+template <class F>
+__device__ __forceinline__ void plane_entries(const PtEntry *tab, int &k, int kend, int z,
+                                              int tx, int ty, F f)
+{
+    while (k < kend && tab[k].z < z) ++k;
+    for (; k < kend && tab[k].z == z; ++k) {
+        const PtEntry en = tab[k];
+        const int xl = en.yx & 0xffff, yl = en.yx >> 16;
+        if (yl == ty && (xl >> 2) == tx) f(xl & 3, en);
+    }
+}
+
+template <int SHAPE, int M, int MODE, int TY>
+__global__ void __launch_bounds__(16 * TY) step3d_kernel(const __grid_constant__ StepParams p)
+{
+    constexpr int HX = round4(M);
+    constexpr int PW = kTX3 + 2 * HX;
+    constexpr int PH = TY + 2 * M;
+    constexpr int PLANE = PW * PH;          // floats copied per plane
+    constexpr int SLOT = (PLANE + 31) & ~31;  // slot stride: 128-byte aligned TMA destinations
+    constexpr int NS = ring_slots<M>();
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t bar[NS];
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int ntile = p.tiles_x * p.tiles_y;
+    const int tile = blockIdx.x % ntile, zc = blockIdx.x / ntile;
+    const int x0 = (tile % p.tiles_x) * kTX3, y0 = (tile / p.tiles_x) * TY;
+    const int zb = zc * p.zchunk;
+    const int ze = min((int)p.nz, zb + p.zchunk);
+    const int L = (ze - zb) + 2 * M;
+
+    int issued = 0;
+    if (tid == 0) {
+        prefetch_tmap(p.tmap);
+        for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (; issued < NS && issued < L; ++issued) {
+            mbar_arrive_expect_tx(&bar[issued], PLANE * 4);
+            tma_load_3d(sm + issued * SLOT, p.tmap, &bar[issued], x0 - HX, y0 - M,
+                        zb - M + issued);
+        }
+    }
+
+    const int xg = x0 + 4 * tx, yg = y0 + ty;
+    const bool colok = xg < p.nx && yg < p.ny;
+    float d2xy[4];
+    {
+        const float d2y = layer_d2(yg, p.phys_lo[1], p.phys_hi[1]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d2xy[j] = layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2y;
+    }
+    int ki = p.inj_ptr ? p.inj_ptr[tile] : 0, kie = p.inj_ptr ? p.inj_ptr[tile + 1] : 0;
+    int ks = p.smp_ptr ? p.smp_ptr[tile] : 0, kse = p.smp_ptr ? p.smp_ptr[tile + 1] : 0;
+
+    const int64_t colo = (int64_t)yg * p.pitch + xg;
+    float4 up_n = make_float4(0.f, 0.f, 0.f, 0.f), kp_n = up_n;
+    if (colok && zb < ze) {
+        up_n = ldg4(p.u_prev + (int64_t)zb * p.plane + colo);
+        kp_n = ldg4(p.kappa + (int64_t)zb * p.plane + colo);
+    }
+    bool ok = true;
+    for (int zi = 0; zi < ze - zb; ++zi) {
+        const int z = zb + zi;
+        const float4 up = up_n, kp = kp_n;
+        if (colok && zi + 1 < ze - zb) {
+            up_n = ldg4(p.u_prev + (int64_t)(z + 1) * p.plane + colo);
+            kp_n = ldg4(p.kappa + (int64_t)(z + 1) * p.plane + colo);
+        }
+        for (int i = (zi == 0 ? 0 : zi + 2 * M); i <= zi + 2 * M; ++i)
+            ok = ok && mbar_wait_bounded(&bar[i % NS], (i / NS) & 1);
+
+        float lap[4] = {0.f, 0.f, 0.f, 0.f};
+        const int yl = M + ty;
+        const float *P0 = sm + ((zi + M) % NS) * SLOT;
+        // in-plane (xy) part of the shape
+#pragma unroll
+        for (int q = 0; q <= M; ++q) {
+            const int E = shape_ext(SHAPE, M, 0, q);
+            const int E4 = round4(E);
+            float win[4 + 2 * HX];
+            const float *rp = P0 + (yl + q) * PW + HX + 4 * tx - E4;
+            const float *rm = P0 + (yl - q) * PW + HX + 4 * tx - E4;
+#pragma unroll
+            for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
+                float4 a = ld4(rp + 4 * i);
+                if (q > 0) {
+                    const float4 b = ld4(rm + 4 * i);
+                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                }
+                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float acc = p.w[q] * win[E4 + j];
+#pragma unroll
+                for (int pp = 1; pp <= E; ++pp)
+                    acc = fmaf(p.w[pp * kWDim + q], win[E4 + j + pp] + win[E4 + j - pp], acc);
+                lap[j] += acc;
+            }
+        }
+        // planes z +- s: the xz-plane line (row y) and the yz-plane column
+#pragma unroll
+        for (int s = 1; s <= M; ++s) {
+            const int E = shape_ext(SHAPE, M, 0, s);
+            const int E4 = round4(E);
+            const float *Pp = sm + ((zi + M + s) % NS) * SLOT;
+            const float *Pm = sm + ((zi + M - s) % NS) * SLOT;
+            float win[4 + 2 * HX];
+            const float *rp = Pp + yl * PW + HX + 4 * tx - E4;
+            const float *rm = Pm + yl * PW + HX + 4 * tx - E4;
+#pragma unroll
+            for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
+                float4 a = ld4(rp + 4 * i);
+                const float4 b = ld4(rm + 4 * i);
+                a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float acc = p.w[s] * win[E4 + j];
+#pragma unroll
+                for (int pp = 1; pp <= E; ++pp)
+                    acc = fmaf(p.w[pp * kWDim + s], win[E4 + j + pp] + win[E4 + j - pp], acc);
+                lap[j] += acc;
+            }
+#pragma unroll
+            for (int qq = 1; qq <= E; ++qq) {
+                const int c = HX + 4 * tx;
+                float4 a = ld4(Pp + (yl + qq) * PW + c);
+                const float4 b = ld4(Pp + (yl - qq) * PW + c);
+                const float4 d = ld4(Pm + (yl + qq) * PW + c);
+                const float4 e = ld4(Pm + (yl - qq) * PW + c);
+                const float wq = p.w[qq * kWDim + s];
+                lap[0] = fmaf(wq, (a.x + b.x) + (d.x + e.x), lap[0]);
+                lap[1] = fmaf(wq, (a.y + b.y) + (d.y + e.y), lap[1]);
+                lap[2] = fmaf(wq, (a.z + b.z) + (d.z + e.z), lap[2]);
+                lap[3] = fmaf(wq, (a.w + b.w) + (d.w + e.w), lap[3]);
+            }
+        }
+
+        const float4 c = ld4(P0 + yl * PW + HX + 4 * tx);
+        const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
+        const float cc[4] = {c.x, c.y, c.z, c.w};
+        const float uu[4] = {up.x, up.y, up.z, up.w};
+        const float kk[4] = {kp.x, kp.y, kp.z, kp.w};
+        float o[4], dv[4], g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            g[j] = p.gcoef * (d2xy[j] + d2z);
+            dv[j] = kk[j] * lap[j];
+            o[j] = (cc[j] - uu[j]) + cc[j] + dv[j] + g[j] * uu[j];
+        }
+        if (p.inj_ptr)
+            plane_entries(p.inj, ki, kie, z, tx, ty, [&](int j, const PtEntry &en) {
+                float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
+                if (MODE == kModeAdjoint) a *= kk[j];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj == j) o[jj] += a;
+            });
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+        if (p.smp_ptr)
+            plane_entries(p.smp, ks, kse, z, tx, ty, [&](int j, const PtEntry &en) {
+                float v = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj == j) v = o[jj];
+                v *= en.scale;
+                if (MODE == kModeAdjoint) v /= kk[j];
+                p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
+            });
+        if (colok) {
+            const int64_t off = (int64_t)z * p.plane + colo;
+            const float4 un = make_float4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<float4 *>(p.u_prev + off) = un;
+            if (MODE == kModeStoreD)
+                *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+            if (MODE == kModeAdjoint) {
+                const float4 d = ldg4(p.dseg_in + off);
+                float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
+                ga.x = fmaf(un.x, d.x, ga.x); ga.y = fmaf(un.y, d.y, ga.y);
+                ga.z = fmaf(un.z, d.z, ga.z); ga.w = fmaf(un.w, d.w, ga.w);
+                *reinterpret_cast<float4 *>(p.gacc + off) = ga;
+            }
+        }
+        // all threads are done with plane zi - M (slot zi % NS): refill it
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(p.status, kStatusTimeout);
+                for (int i = zi + 2 * M + 1; i < issued; ++i)
+                    mbar_wait_bounded(&bar[i % NS], (i / NS) & 1, 100000000LL);
+            }
+            return;
+        }
+        if (tid == 0 && issued < L) {
+            const int slot = issued % NS;
+            mbar_arrive_expect_tx(&bar[slot], PLANE * 4);
+            tma_load_3d(sm + slot * SLOT, p.tmap, &bar[slot], x0 - HX, y0 - M, zb - M + issued);
+            ++issued;
+        }
+    }
+}
+
+using KernelFn = void (*)(const StepParams);
+
+template <int SHAPE, int M, int TY>
+KernelFn pick3(int mode)
+{
+    switch (mode) {
+    case kModeForward: return step3d_kernel<SHAPE, M, kModeForward, TY>;
+    case kModeStoreD: return step3d_kernel<SHAPE, M, kModeStoreD, TY>;
+    default: return step3d_kernel<SHAPE, M, kModeAdjoint, TY>;
+    }
+}
+
+KernelFn lookup3(int shape, int M, int ty, int mode)
+{
+#define FDW_C(S, MM, TT) \
+    if (shape == S && M == MM && ty == TT) return pick3<S, MM, TT>(mode);
+    FDW_C(FD_CROSS, 1, 16) FDW_C(FD_CROSS, 2, 16) FDW_C(FD_CROSS, 3, 16) FDW_C(FD_CROSS, 4, 16)
+    FDW_C(FD_CROSS, 6, 8) FDW_C(FD_CROSS, 8, 8)
+    FDW_C(FD_RHOMBUS, 2, 16) FDW_C(FD_RHOMBUS, 3, 16) FDW_C(FD_RHOMBUS, 4, 16)
+    FDW_C(FD_RHOMBUS, 6, 8) FDW_C(FD_RHOMBUS, 8, 8)
+    FDW_C(FD_SQUARE, 2, 16) FDW_C(FD_SQUARE, 4, 16)
+#undef FDW_C
+    return nullptr;
+}
+
+}  // namespace
+
+int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t nz, Variant *v)
+{
+    v->dim = 3;
+    v->shape = shape;
+    v->M = M;
+    v->N = N;
+    v->generic = 0;
+    int ty = M <= 4 ? 16 : 8;
+    if (!lookup3(shape, M, ty, 0)) return FD_ERR_UNSUPPORTED;
+    v->tx = kTX3;
+    v->tz = ty;
+    v->threads = 16 * ty;
+    const int HX = round4(M);
+    v->box[0] = kTX3 + 2 * HX;
+    v->box[1] = ty + 2 * M;
+    v->box[2] = 1;
+    v->smem = (size_t)(2 * M + 1 + kPF) * ((v->box[0] * v->box[1] + 31) & ~31) * sizeof(float);
+    (void)nx; (void)ny; (void)nz;
+    return 0;
+}
+
+cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s)
+{
+    KernelFn fn = lookup3(v.shape, v.M, v.tz, mode);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e =
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    if (e != cudaSuccess) return e;
+    const int grid = p.tiles_x * p.tiles_y * p.nz_chunks;
+    if (grid <= 0) return cudaSuccess;
+    fn<<<grid, v.threads, v.smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace fdw

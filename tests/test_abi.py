@@ -1,0 +1,137 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+declared in include/fdwave.h, and its host-side entry points (weights, CFL
+bound, Ricker wavelet, plan validation, workspace sizing) agree with the FP64
+oracle and reject bad arguments."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2606_04882_gb300 as F
+from oracle import physics as P
+from oracle import stencil as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2606_04882_gb300 import build
+    build.build()
+
+
+def _declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "fdwave.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char|double|size_t)\s*\*?\s*(fd_\w+)\s*\(",
+                       txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared_symbols()
+    assert len(names) >= 15, names
+    L = F.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    # and the binding exposes the same names
+    for n in names:
+        assert n in F._SIGS, n
+
+
+@pytest.mark.parametrize("dim,shape,M,N,scheme", [
+    (2, "cross", 1, 0, "spatte"), (2, "cross", 4, 0, "spatte"), (2, "cross", 8, 0, "spatte"),
+    (3, "cross", 4, 0, "spatte"), (3, "cross", 8, 0, "spatte"), (2, "cross", 16, 0, "spatte"),
+    (2, "rhombus", 4, 0, "dispte"), (2, "cross_rhombus", 5, 3, "dispte"),
+    (2, "square", 3, 0, "dispte"), (2, "cross_square", 4, 2, "dispte"),
+    (2, "cross", 4, 0, "specte_theta"), (2, "rhombus", 4, 0, "dispte_theta"),
+    (2, "cross", 4, 0, "displs"), (2, "rhombus", 4, 0, "displs"), (2, "square", 2, 0, "specls"),
+    (3, "rhombus", 4, 0, "displs"), (2, "cross", 8, 0, "displs"),
+])
+def test_weights_and_cfl_match_oracle(dim, shape, M, N, scheme):
+    C = 0.3
+    d = F.stencil_desc(dim, shape, M, N, scheme, courant=C)
+    keys, mult, w = F.fd_weights(d)
+    ow = S.weights(dim, shape, M, N, scheme, C=C)
+    orbs = S.orbits(S.point_set(dim, shape, M, N))
+    assert len(keys) == len(ow)
+    scale = max(abs(x) for x in w)
+    # least-squares design matrices have condition numbers up to ~1e7 (cross 8)
+    tol = (1e-9 if M <= 4 else 1e-6) if scheme in ("displs", "specls") else 1e-12
+    for i, k in enumerate(keys):
+        kk = tuple(int(x) for x in k[:dim])
+        assert mult[i] == len(orbs[kk])
+        assert abs(w[i] - ow[kk]) <= tol * scale, (kk, w[i], ow[kk])
+    c = F.fd_cfl_limit(d)
+    oc = S.cfl_limit(S.expand(dim, shape, M, N, ow), dim)
+    assert abs(c - oc) < 1e-7 * oc
+
+
+def test_square8_displs_within_ls_cutoff_agreement():
+    # the most ill-conditioned LS problem: both solvers truncate at the same
+    # relative cutoff and agree to ~1e-6
+    d = F.stencil_desc(2, "square", 8, 0, "displs", courant=0.3)
+    _, _, w = F.fd_weights(d)
+    ow = S.weights(2, "square", 8, 0, "displs", C=0.3)
+    keys, _, _ = F.fd_weights(d)
+    err = max(abs(w[i] - ow[tuple(int(x) for x in k[:2])]) for i, k in enumerate(keys))
+    assert err < 1e-6 * max(abs(x) for x in w)
+
+
+def test_ricker_matches_oracle():
+    f0, dt, nt = 15.0, 1e-3, 300
+    a = F.fd_ricker(f0, dt, nt)
+    b = P.ricker(f0, nt, dt)
+    assert a.dtype == np.float32
+    assert np.max(np.abs(a - b)) < 1e-7
+
+
+def test_plan_validation_and_stability_check():
+    d = F.stencil_desc(2, "cross", 4)
+    cm = F.fd_cfl_limit(d)
+    h, v = 10.0, 3000.0
+    ok = F.Plan((50, 60), h, 0.99 * cm * h / v, 10, 5, v, d)
+    inf = ok.info()
+    assert tuple(inf.padded) == (60, 1, 70)
+    assert inf.pitch % 32 == 0 and inf.pitch >= 70
+    assert abs(inf.courant_max - cm) < 1e-12
+    with pytest.raises(F.FdError) as e:
+        F.Plan((50, 60), h, 1.01 * cm * h / v, 10, 5, v, d)
+    assert e.value.code == F.FD_ERR_UNSTABLE
+    with pytest.raises(F.FdError) as e:
+        F.Plan((50, 60), -1.0, 1e-3, 10, 5, v, d)
+    assert e.value.code == F.FD_ERR_ARG
+    bad = F.stencil_desc(2, "cross_rhombus", 4, 7, "dispte")
+    with pytest.raises(F.FdError) as e:
+        F.fd_weights(bad)
+    assert e.value.code == F.FD_ERR_ARG
+    with pytest.raises(F.FdError) as e:
+        F.fd_weights(F.stencil_desc(3, "cross", 4, 0, "specte_theta"))
+    assert e.value.code == F.FD_ERR_UNSUPPORTED
+    with pytest.raises(F.FdError) as e:   # 3D cross-square kernels are not provided
+        F.Plan((20, 20, 20), h, 1e-4, 5, 2, v, F.stencil_desc(3, "cross_square", 4, 2, "dispte", courant=0.1))
+    assert e.value.code == F.FD_ERR_UNSUPPORTED
+
+
+def test_taylor_rhombus_reduces_to_cross_kernel():
+    d = F.stencil_desc(2, "rhombus", 4, 0, "spatte")
+    p = F.Plan((40, 40), 10.0, 5e-4, 4, 4, 3000.0, d)
+    assert p.info().effective_shape == F.SHAPES["cross"]
+    d = F.stencil_desc(2, "rhombus", 4, 0, "displs", courant=0.15)
+    p = F.Plan((40, 40), 10.0, 5e-4, 4, 4, 3000.0, d)
+    assert p.info().effective_shape == F.SHAPES["rhombus"]
+
+
+def test_workspace_sizes():
+    d = F.stencil_desc(3, "cross", 4)
+    p = F.Plan((30, 31, 32), 10.0, 1e-3, 100, 6, 3000.0, d)
+    f = p.forward_workspace_size(1, 100)
+    g = p.gradient_workspace_size(1, 100, 10)
+    inf = p.info()
+    field = inf.padded[0] * inf.padded[1] * inf.pitch * 4
+    assert f >= 3 * field
+    # gradient: 4 buffers + kappa + gacc + 2*10 checkpoints + 10 segment fields
+    assert g >= (6 + 20 + 10) * field
+    assert p.gradient_workspace_size(1, 100, 5) > g

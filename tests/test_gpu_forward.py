@@ -1,0 +1,131 @@
+"""Forward parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance: relative L2 <= 1e-4 on traces and final wavefields (the contract
+for FP32 wavefields after the full run).  Small cases span several tiles with
+ragged tails in every axis; the homogeneous 201^2 workload runs at full size
+and length."""
+import numpy as np
+import pytest
+
+from gpu_cases import Case, rel_l2
+from workloads import homogeneous_2d, smooth_velocity
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_04882_gb300 import build
+    build.build()
+
+
+def _case2d(shape, M, N, scheme, nz=131, nx=157, nb=10, nt=150, seed=11):
+    vel = smooth_velocity((nz, nx), seed, 1500.0, 3000.0, sigma=4.0)
+    rng = np.random.default_rng(seed)
+    src = np.array([[nz // 2, nx // 3], [5, nx - 3]])
+    rec = np.stack([rng.integers(0, nz, 40), rng.integers(0, nx, 40)], axis=1)
+    rec[0] = (0, 0)
+    rec[1] = (nz - 1, nx - 1)
+    return Case(vel, 10.0, nt, nb, 3000.0, shape, M, N, scheme, src=src, rec=rec, f0=20.0)
+
+
+@pytest.mark.parametrize("shape,M,N,scheme", [
+    ("cross", 1, 0, "spatte"), ("cross", 2, 0, "spatte"), ("cross", 4, 0, "spatte"),
+    ("cross", 8, 0, "spatte"), ("cross", 3, 0, "dispte"), ("cross", 12, 0, "spatte"),
+    ("rhombus", 2, 0, "displs"), ("rhombus", 4, 0, "displs"), ("rhombus", 8, 0, "displs"),
+    ("square", 2, 0, "displs"), ("square", 4, 0, "displs"), ("square", 8, 0, "displs"),
+    ("rhombus", 5, 0, "dispte"), ("cross_rhombus", 4, 2, "dispte"),
+    ("cross_square", 4, 2, "displs"), ("cross", 4, 0, "specte_theta"),
+])
+def test_forward_2d_matches_oracle(shape, M, N, scheme):
+    c = _case2d(shape, M, N, scheme)
+    tr, st, rc = c.gpu_forward()
+    assert rc == 0
+    otr, ost = c.oracle_forward(threads=8)
+    assert rel_l2(tr, otr) < TOL
+    assert rel_l2(st[0], ost[0]) < TOL and rel_l2(st[1], ost[1]) < TOL
+
+
+@pytest.mark.parametrize("shape,M,scheme", [
+    ("cross", 1, "spatte"), ("cross", 2, "spatte"), ("cross", 4, "spatte"), ("cross", 8, "spatte"),
+    ("rhombus", 2, "displs"), ("rhombus", 4, "displs"), ("cross", 3, "spatte"),
+    ("square", 2, "displs"), ("cross", 6, "spatte"),
+])
+def test_forward_3d_matches_oracle(shape, M, scheme):
+    nz, ny, nx, nb = 38, 45, 52, 8
+    vel = smooth_velocity((nz, ny, nx), 7, 1500.0, 3000.0, sigma=3.0)
+    rng = np.random.default_rng(3)
+    rec = np.stack([rng.integers(0, n, 60) for n in (nz, ny, nx)], axis=1)
+    src = np.array([[nz // 2, ny // 2, nx // 2], [2, 3, nx - 2]])
+    c = Case(vel, 10.0, 70, nb, 3000.0, shape, M, 0, scheme, src=src, rec=rec, f0=25.0)
+    tr, st, rc = c.gpu_forward()
+    assert rc == 0
+    otr, ost = c.oracle_forward(threads=8)
+    assert rel_l2(tr, otr) < TOL
+    assert rel_l2(st[0], ost[0]) < TOL
+
+
+def test_homogeneous_201_full_run():
+    """The 201^2 homogeneous workload (h = 10 m, v = 1500 m/s, Cross(4)
+    Taylor, dt = 0.5 CFL, 500 steps, 15 Hz Ricker at the centre, 201
+    receivers at 20 m depth, 20-node sponge) at full size and length."""
+    pr = homogeneous_2d()
+    c = Case(pr.vel, pr.h, pr.nt, pr.nb, pr.vmax, "cross", 4, 0, "spatte", src=pr.src,
+             rec=pr.rec, f0=pr.f0)
+    tr, st, rc = c.gpu_forward()
+    assert rc == 0
+    otr, ost = c.oracle_forward(threads=8)
+    assert rel_l2(tr, otr) < TOL
+    assert rel_l2(st[0], ost[0]) < TOL
+
+
+def test_restart_from_state_is_bitwise_and_matches_oracle():
+    c = _case2d("cross", 4, 0, "spatte", nt=120)
+    tr, st, rc = c.gpu_forward()
+    tra, sta, _ = c.gpu_forward(nt=50)
+    trb, stb, _ = c.gpu_forward(nt=70, state_in=sta, t0=50)
+    assert np.array_equal(tr, np.concatenate([tra, trb]))
+    assert np.array_equal(st, stb)
+    # one GPU step from a mid-run state equals one oracle step from that state
+    otr, ost = c.oracle_forward(nt=70, state_in=sta, t0=50)
+    assert rel_l2(trb, otr) < TOL and rel_l2(stb[0], ost[0]) < TOL
+
+
+def test_edge_cases():
+    # grid smaller than one tile, no sponge, source and receiver on corners
+    vel = np.full((5, 7), 2000.0, np.float32)
+    c = Case(vel, 10.0, 20, 0, 2000.0, "cross", 2, 0, "spatte", src=[[0, 0]], rec=[[4, 6], [0, 0], [0, 0]])
+    tr, st, rc = c.gpu_forward()
+    otr, ost = c.oracle_forward()
+    assert rc == 0 and rel_l2(tr, otr) < TOL and rel_l2(st[0], ost[0]) < TOL
+    assert np.array_equal(tr[:, 1], tr[:, 2])        # duplicated receiver
+    # stencil radius larger than the grid
+    vel = np.full((6, 9), 2000.0, np.float32)
+    c = Case(vel, 10.0, 15, 0, 2000.0, "cross", 8, 0, "spatte", src=[[3, 4]], rec=[[1, 1]])
+    tr, st, rc = c.gpu_forward()
+    otr, ost = c.oracle_forward()
+    assert rel_l2(tr, otr) < TOL and rel_l2(st[0], ost[0]) < TOL
+    # no sources, no receivers, non-zero initial state
+    vel = smooth_velocity((40, 50), 1, 1500.0, 2500.0)
+    c = Case(vel, 10.0, 30, 4, 2500.0, "rhombus", 4, 0, "displs", src=np.zeros((0, 2)), rec=None)
+    st0 = np.random.default_rng(0).standard_normal((2, 48, 58)).astype(np.float32)
+    _, st, rc = c.gpu_forward(state_in=st0)
+    _, ost = c.oracle_forward(state_in=st0)
+    assert rc == 0 and rel_l2(st[0], ost[0]) < TOL
+    # zero steps returns the initial state
+    c0 = Case(vel, 10.0, 0, 4, 2500.0, "cross", 4, src=np.zeros((0, 2)))
+    _, st, _ = c0.gpu_forward(state_in=st0)
+    assert np.array_equal(st, st0)
+
+
+def test_velocity_above_vmax_is_reported():
+    import paper_2606_04882_gb300 as F
+    vel = np.full((20, 20), 2000.0, np.float32)
+    vel[5, 5] = 2600.0
+    c = Case(vel, 10.0, 5, 2, 2500.0, "cross", 2, src=[[10, 10]], rec=[[1, 1]])
+    _, _, rc = c.gpu_forward()
+    assert rc == F.FD_ERR_UNSTABLE
