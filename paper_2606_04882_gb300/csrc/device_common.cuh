@@ -115,6 +115,18 @@ __device__ __forceinline__ float layer_d2(int64_t i, int64_t lo, int64_t hi)
     return static_cast<float>(d * d);
 }
 
+// Leapfrog bracket with explicit rounding (no contraction), so every kernel
+// mode (forward, forward + D store, adjoint) rounds identically:
+//   o = ((u - u_prev) + u) + kappa*lap + g*u_prev = 2u - (1-g)u_prev + kappa lap.
+// Returns D = kappa * lap.
+__device__ __forceinline__ float step_update(float u, float up, float k, float lap, float g,
+                                             float &o)
+{
+    const float d = __fmul_rn(k, lap);
+    o = __fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(u, up), u), d), __fmul_rn(g, up));
+    return d;
+}
+
 __device__ __forceinline__ float4 ld4(const float *p)
 {
     return *reinterpret_cast<const float4 *>(p);

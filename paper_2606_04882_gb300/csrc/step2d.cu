@@ -125,9 +125,7 @@ __global__ void __launch_bounds__(kThreads) step2d_kernel(const __grid_constant_
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             g[j] = p.gcoef * (d2x[j] + d2z);
-            dv[j] = kk[j] * lap[j];
-            // (u - u_prev) + u + kappa lap, with (1 - g) u_prev for the sponge
-            o[j] = (cc[j] - uu[j]) + cc[j] + dv[j] + g[j] * uu[j];
+            dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
         }
         // injection inside the bracket; adjoint residuals are scaled by kappa
         if (p.inj_ptr)
@@ -227,8 +225,7 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
         }
         const float c = sm[zl * SW + xc];
         gm[j] = p.gcoef * (layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2z);
-        dv[j] = kk[j] * lap;
-        o[j] = (c - uu[j]) + c + dv[j] + gm[j] * uu[j];
+        dv[j] = step_update(c, uu[j], kk[j], lap, gm[j], o[j]);
     }
     float4 br = make_float4(o[0], o[1], o[2], o[3]);
     if (p.inj_ptr)

@@ -176,8 +176,7 @@ __global__ void __launch_bounds__(16 * TY) step3d_kernel(const __grid_constant__
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             g[j] = p.gcoef * (d2xy[j] + d2z);
-            dv[j] = kk[j] * lap[j];
-            o[j] = (cc[j] - uu[j]) + cc[j] + dv[j] + g[j] * uu[j];
+            dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
         }
         if (p.inj_ptr)
             plane_entries(p.inj, ki, kie, z, tx, ty, [&](int j, const PtEntry &en) {
