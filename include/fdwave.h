@@ -256,6 +256,32 @@ int fd_forward_batched_workspace_size(int nshots, const fd_shot *shots, size_t *
 int fd_forward_batched(int nshots, const fd_shot *shots, void *ws_d, size_t ws_bytes,
                        void *stream);
 
+/*
+ * fd_forward_noalloc - fd_forward for callers that cannot allocate device
+ * memory (an allocator that owns all device memory, a real-time loop where an
+ * allocation would stall, a plugin host that hands out none).  The paper has
+ * no counterpart; this is a deployment convenience.
+ * Arguments are those of fd_forward without the workspace: the scratch comes
+ * from a static device array of 32 MiB compiled into the library, which every
+ * GPU that loads the library holds until the process exits.  The call
+ * allocates no device memory.
+ *   - Problems whose forward workspace (fd_forward_workspace_size) exceeds
+ *     32 MiB are rejected with FD_ERR_NOMEM before any device work.
+ *   - The first call on a device resolves the array's address on that device
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents.  Each
+ *     call clears what must start at zero, but calls that overlap on the GPU
+ *     (other streams, other host threads, other plans) race on it: serialise
+ *     them.
+ *   - Device status bits of these calls are not retrievable by fd_status_read
+ *     (the caller has no workspace pointer); host-side errors are returned.
+ */
+int fd_forward_noalloc(fd_plan *plan, int model_kind, const float *model_d,
+                       int nsrc, const int64_t *src_idx, const float *wavelet_d,
+                       int nrec, const int64_t *rec_idx, float *traces_d,
+                       const float *state_in_d, float *state_out_d, void *stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char *fd_last_error(void);
 

@@ -86,6 +86,7 @@ _SIGS = {
     "fd_adjoint_gradient": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _P, _P, _SZ, _P]),
     "fd_forward_batched_workspace_size": (_I, [_I, _P, _P]),
     "fd_forward_batched": (_I, [_I, _P, _P, _SZ, _P]),
+    "fd_forward_noalloc": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P]),
     "fd_last_error": (ctypes.c_char_p, []),
     "fd_version": (ctypes.c_char_p, []),
 }
@@ -247,6 +248,21 @@ def fd_forward(plan: Plan, model, src_idx: np.ndarray, wavelet, rec_idx: np.ndar
                             len(rec_idx), rec_idx.ctypes.data if len(rec_idx) else None,
                             _addr(traces), _addr(state_in), _addr(state_out), _addr(ws),
                             ws.numel(), _stream_ptr(stream)))
+
+
+def fd_forward_noalloc(plan: Plan, model, src_idx: np.ndarray, wavelet, rec_idx: np.ndarray, traces,
+                       state_in=None, state_out=None, model_kind: int = FD_MODEL_VELOCITY,
+                       stream=None):
+    """fd_forward for callers that cannot allocate device memory: the library
+    uses its own 32 MiB static device scratch (see include/fdwave.h); larger
+    problems raise FdError(FD_ERR_NOMEM).  Calls must not overlap on the GPU."""
+    src_idx = np.ascontiguousarray(src_idx, np.int64)
+    rec_idx = np.ascontiguousarray(rec_idx, np.int64)
+    _check(lib().fd_forward_noalloc(plan.ptr, model_kind, _addr(model), len(src_idx),
+                                    src_idx.ctypes.data if len(src_idx) else None, _addr(wavelet),
+                                    len(rec_idx), rec_idx.ctypes.data if len(rec_idx) else None,
+                                    _addr(traces), _addr(state_in), _addr(state_out),
+                                    _stream_ptr(stream)))
 
 
 def fd_status_read(plan: Plan, ws, stream=None) -> int:
