@@ -33,7 +33,11 @@ enum Mode : int {
 
 // Parameters of one step launch (2D and 3D kernels).
 struct StepParams {
-    const CUtensorMap *tmap;   // tensor map of the field read by the stencil (global memory)
+    const CUtensorMap *tmap;   // tensor map of the field read by the stencil (halo box)
+    const CUtensorMap *tmap_cur_t;    // same field, tile box (no halo)      [3D cross]
+    const CUtensorMap *tmap_prev_t;   // u_prev, tile box                     [3D cross]
+    const CUtensorMap *tmap_kappa_t;  // kappa, tile box                      [3D cross]
+    const float *u_cur;        // the field read by the stencil
     float *u_prev;             // in: older field, out: new field (same buffer)
     const float *kappa;        // (v tau / h)^2 on the padded grid
     int64_t nx, ny, nz;        // padded sizes (ny = 1 in 2D)
@@ -60,37 +64,7 @@ struct StepParams {
     const float *dseg_in;      // kModeAdjoint: D^{j-1}
     float *gacc;               // kModeAdjoint: accumulator (same layout as fields)
     int *status;
-    int shot;                  // batched: index into shot tables (unused single-shot)
     float w[kWDim * kWDim];    // symmetric weight table W[p][q] = a_orbit(max, min)
-};
-
-// Batched 2D: one launch per step over all shots' tiles.
-struct ShotDev {
-    const CUtensorMap *tmap_a, *tmap_b;     // maps of buffers a and b
-    float *buf_a, *buf_b;
-    const float *kappa;
-    int64_t nx, nz, pitch;
-    int64_t phys_lo[2], phys_hi[2];
-    int tiles_x, tiles_z;
-    int tile_base;                          // first global tile id of this shot
-    const int32_t *inj_ptr;
-    const PtEntry *inj;
-    const float *inj_series;
-    int inj_ncol;
-    const int32_t *smp_ptr;
-    const PtEntry *smp;
-    float *smp_out;
-    int smp_ncol;
-};
-
-struct BatchParams {
-    const ShotDev *shots;
-    const int32_t *tile_shot;               // global tile id -> shot
-    int ntiles;
-    int step;                               // time step n (selects buffer parity)
-    float gcoef;
-    int *status;
-    float w[kWDim * kWDim];
 };
 
 // Kernel variant descriptor chosen by the plan.
@@ -100,7 +74,8 @@ struct Variant {
     int tx, tz;        // 2D tile: columns, rows of output per CTA; 3D: x, y
     int threads;
     size_t smem;
-    int box[3];        // TMA box (x, y, z)
+    int box[3];        // TMA box with halo (x, y, z)
+    int tbox[2];       // TMA tile box without halo (x, y) [3D cross]
 };
 
 // Host launchers (defined in the .cu files).
@@ -108,8 +83,6 @@ int select_variant_2d(int shape, int M, int N, int64_t nx, int64_t nz, Variant *
 int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t nz, Variant *v);
 cudaError_t launch_step2d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
 cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
-cudaError_t launch_batch2d(const Variant &v, const BatchParams &p, int ntiles, cudaStream_t s);
-int batch_supported(const Variant &v);
 
 // aux kernels
 cudaError_t launch_prep_kappa(const float *model, int kind, float *kappa, int dim,

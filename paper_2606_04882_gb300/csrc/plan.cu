@@ -90,7 +90,7 @@ Layout make_layout(const fd_plan *p, int nsrc, int nrec, bool grad, int kseg)
     const size_t fb = up(p->field * sizeof(float));
     size_t o = 0;
     L.status = o; o += kAlign;
-    L.n_tmaps = grad ? 4 : 2;
+    L.n_tmaps = 2 * (grad ? 4 : 2) + 1;   // (halo box, tile box) per buffer + kappa tile box
     L.tmaps = o; o += up(L.n_tmaps * sizeof(CUtensorMap));
     L.kappa = o; o += fb;
     for (int i = 0; i < (grad ? 4 : 2); ++i) { L.buf[i] = o; o += fb; }
@@ -254,7 +254,8 @@ cudaError_t launch(const fd_plan *p, int mode, const StepParams &sp, cudaStream_
     return p->prob.dim == 2 ? launch_step2d(p->var, mode, sp, s) : launch_step3d(p->var, mode, sp, s);
 }
 
-int encode_field_map(const fd_plan *p, CUtensorMap *map, const float *base)
+// Tensor map of one field buffer: halo box (tile = false) or tile box.
+int encode_field_map(const fd_plan *p, CUtensorMap *map, const float *base, bool tile)
 {
     int64_t dims[3], str[2];
     int box[3];
@@ -266,8 +267,22 @@ int encode_field_map(const fd_plan *p, CUtensorMap *map, const float *base)
     }
     dims[0] = p->pad[2]; dims[1] = p->pad[1]; dims[2] = p->pad[0];
     str[0] = p->pitch * 4; str[1] = p->plane * 4;
-    box[0] = p->var.box[0]; box[1] = p->var.box[1]; box[2] = 1;
+    if (tile) {
+        box[0] = p->var.tbox[0]; box[1] = p->var.tbox[1];
+    } else {
+        box[0] = p->var.box[0]; box[1] = p->var.box[1];
+    }
+    box[2] = 1;
     return encode_tmap(map, base, 3, dims, str, box);
+}
+
+// Point the step parameters at buffer `cur` (stencil input) and `prev` (u_prev).
+void bind_maps(StepParams &sp, const CUtensorMap *maps, int nbuf, int cur, int prev)
+{
+    sp.tmap = maps + 2 * cur;
+    sp.tmap_cur_t = maps + 2 * cur + 1;
+    sp.tmap_prev_t = maps + 2 * prev + 1;
+    sp.tmap_kappa_t = maps + 2 * nbuf;
 }
 
 int check_common(const fd_plan *p, int model_kind, const float *model, int nsrc,
@@ -419,12 +434,17 @@ int upload_tables(fd_plan *p, const Layout &L, char *ws, const Tables &T, cudaSt
 
 int upload_maps(fd_plan *p, const Layout &L, char *ws, int nbuf, cudaStream_t s)
 {
-    std::vector<CUtensorMap> maps(nbuf);
-    for (int i = 0; i < nbuf; ++i) {
-        int r = encode_field_map(p, &maps[i], reinterpret_cast<const float *>(ws + L.buf[i]));
-        if (r) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", r);
-    }
-    FDW_CK(cudaMemcpyAsync(ws + L.tmaps, maps.data(), nbuf * sizeof(CUtensorMap),
+    std::vector<CUtensorMap> maps(2 * nbuf + 1);
+    for (int i = 0; i < nbuf; ++i)
+        for (int t = 0; t < 2; ++t) {
+            int r = encode_field_map(p, &maps[2 * i + t], reinterpret_cast<const float *>(ws + L.buf[i]),
+                                     t == 1 && p->prob.dim == 3);
+            if (r) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", r);
+        }
+    int r = encode_field_map(p, &maps[2 * nbuf], reinterpret_cast<const float *>(ws + L.kappa),
+                             p->prob.dim == 3);
+    if (r) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", r);
+    FDW_CK(cudaMemcpyAsync(ws + L.tmaps, maps.data(), maps.size() * sizeof(CUtensorMap),
                            cudaMemcpyHostToDevice, s));
     return FD_OK;
 }
@@ -516,7 +536,8 @@ extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int ns
     }
     for (int n = 0; n < p->prob.nt; ++n) {
         const int cur = n & 1;
-        sp.tmap = maps + cur;
+        bind_maps(sp, maps, 2, cur, cur ^ 1);
+        sp.u_cur = cur ? B : A;
         sp.u_prev = cur ? A : B;
         sp.step = n;
         FDW_CK(launch(p, kModeForward, sp, s));
@@ -603,7 +624,8 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
             FDW_CK(cudaMemcpyAsync(ck + (size_t)(2 * c) * fb, buf[cur], fb, cudaMemcpyDeviceToDevice, s));
             FDW_CK(cudaMemcpyAsync(ck + (size_t)(2 * c + 1) * fb, buf[cur ^ 1], fb, cudaMemcpyDeviceToDevice, s));
         }
-        sp.tmap = maps + cur;
+        bind_maps(sp, maps, 4, cur, cur ^ 1);
+        sp.u_cur = buf[cur];
         sp.u_prev = buf[cur ^ 1];
         sp.step = n;
         FDW_CK(launch(p, kModeForward, sp, s));
@@ -617,7 +639,8 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
         bind_fwd(false);
         for (int n = k0; n < k1; ++n) {
             const int cur = (n - k0) & 1;
-            sp.tmap = maps + cur;
+            bind_maps(sp, maps, 4, cur, cur ^ 1);
+            sp.u_cur = buf[cur];
             sp.u_prev = buf[cur ^ 1];
             sp.step = n;
             sp.dseg_out = reinterpret_cast<float *>(dseg + (size_t)(n - k0) * fb);
@@ -635,7 +658,8 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
         sp.gacc = gacc;
         for (int j = k1; j > k0; --j, ++t) {
             const int cur = 2 + (t & 1);
-            sp.tmap = maps + cur;
+            bind_maps(sp, maps, 4, cur, cur ^ 1);
+            sp.u_cur = buf[cur];
             sp.u_prev = buf[cur ^ 1];
             sp.step = j - 1;
             sp.dseg_in = reinterpret_cast<const float *>(dseg + (size_t)(j - 1 - k0) * fb);
@@ -745,7 +769,8 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         for (int i = 0; i < nshots && ce == cudaSuccess; ++i) {
             StepParams &sp = sps[i];
             const int cur = n & 1;
-            sp.tmap = mp[i] + cur;
+            bind_maps(sp, mp[i], 2, cur, cur ^ 1);
+            sp.u_cur = cur ? Bs[i] : As[i];
             sp.u_prev = cur ? As[i] : Bs[i];
             sp.step = n;
             ce = launch(shots[i].plan, kModeForward, sp, cs);

@@ -243,12 +243,261 @@ KernelFn pick3(int mode)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Cross stencils: warp-specialised TMA pipeline, z-arm in a register queue.
+//
+// One producer warp streams, for every plane z of the chunk, one ring slot
+// holding: the u_cur plane with its x/y halo (x and y arms, centre), the
+// u_prev and kappa tiles of plane z, and the u_cur tile of plane z+M (the
+// newest entry of the z-arm queue).  Slots are guarded by a full and an empty
+// mbarrier each, so consumer warps run ahead of one another by up to the
+// ring depth; there is no block-wide barrier in the plane loop.  Consumers
+// keep the 2M+1 centre values of their column in a register queue; the loop
+// is unrolled by the queue length so queue indices are compile-time.  The
+// first 2M slots of a chunk carry only queue entries (planes zb-M .. zb+M-1).
+// Every wait is bounded; on a time-out the block sets the status bit, the
+// producer waits (bounded) for its copies in flight, and the block returns.
+// ---------------------------------------------------------------------------
+template <int M, int TY>
+struct CrossCfg {
+    static constexpr int HX = round4(M);
+    static constexpr int PW = kTX3 + 2 * HX;
+    static constexpr int PH = TY + 2 * M;
+    static constexpr int AEL = (PW * PH + 31) & ~31;      // halo plane (floats, padded)
+    static constexpr int TEL = kTX3 * TY;                 // tile (floats, multiple of 32)
+    static constexpr int SLOT = AEL + 3 * TEL;            // A | u_prev | kappa | queue tile
+    static constexpr int NR = 4;                          // ring depth
+    static constexpr int NCW = TY / 2;                    // consumer warps
+    static constexpr int THREADS = 16 * TY + 32;
+    static constexpr size_t SMEM = (size_t)NR * SLOT * sizeof(float);
+};
+
+template <int M, int MODE, int TY>
+__global__ void __launch_bounds__(CrossCfg<M, TY>::THREADS, TY == 16 ? 2 : 3)
+step3d_cross(const __grid_constant__ StepParams p)
+{
+    using C = CrossCfg<M, TY>;
+    constexpr int HX = C::HX, PW = C::PW, PH = C::PH;
+    constexpr int NR = C::NR, SLOT = C::SLOT;
+    constexpr int QL = 2 * M + 1;
+    constexpr uint32_t BYTES_FULL = (PW * PH + 3 * C::TEL) * 4;
+    constexpr uint32_t BYTES_Q = C::TEL * 4;
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t full[NR], empty[NR];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int ntile = p.tiles_x * p.tiles_y;
+    const int tile = blockIdx.x % ntile, zc = blockIdx.x / ntile;
+    const int x0 = (tile % p.tiles_x) * kTX3, y0 = (tile / p.tiles_x) * TY;
+    const int zb = zc * p.zchunk;
+    const int nz = (int)p.nz;
+    const int ze = min(nz, zb + p.zchunk);
+    const int L = ze - zb;            // planes computed
+    const int S = L + 2 * M;          // slots streamed (the first 2M carry queue tiles only)
+
+    if (tid == 0) {
+        for (int i = 0; i < NR; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], C::NCW);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == C::NCW) {
+        // ------------------------------ producer ------------------------------
+        if (lane != 0) return;
+        prefetch_tmap(p.tmap);
+        prefetch_tmap(p.tmap_cur_t);
+        prefetch_tmap(p.tmap_prev_t);
+        prefetch_tmap(p.tmap_kappa_t);
+        volatile int *abort_v = &abort_flag;
+        int slot = 0;
+        int s = 0;
+        for (; s < S; ++s) {
+            // reuse of a slot waits for the consumers' release of stream index s - NR,
+            // i.e. the completion of empty phase s / NR - 1
+            if (s >= NR && !mbar_wait_bounded(&empty[slot], (uint32_t)((s / NR - 1) & 1))) {
+                atomicOr(p.status, kStatusTimeout);
+                *abort_v = 1;
+                break;
+            }
+            if (*abort_v) break;
+            float *dst = sm + slot * SLOT;
+            const int zq = zb + s - M;                  // queue plane carried by this slot
+            if (s < 2 * M) {
+                mbar_arrive_expect_tx(&full[slot], BYTES_Q);
+            } else {
+                const int z = zb + s - 2 * M;
+                mbar_arrive_expect_tx(&full[slot], BYTES_FULL);
+                tma_load_3d(dst, p.tmap, &full[slot], x0 - HX, y0 - M, z);
+                tma_load_3d(dst + C::AEL, p.tmap_prev_t, &full[slot], x0, y0, z);
+                tma_load_3d(dst + C::AEL + C::TEL, p.tmap_kappa_t, &full[slot], x0, y0, z);
+            }
+            tma_load_3d(dst + C::AEL + 2 * C::TEL, p.tmap_cur_t, &full[slot], x0, y0, zq);
+            if (++slot == NR) slot = 0;
+        }
+        if (*abort_v) {   // let copies already issued land before the block exits
+            for (int i = max(0, s - NR); i < s; ++i)
+                mbar_wait_bounded(&full[i % NR], (i / NR) & 1, 100000000LL);
+        }
+        return;
+    }
+
+    // ------------------------------- consumers --------------------------------
+    const int ty = tid >> 4, tx = tid & 15;
+    const int xg = x0 + 4 * tx, yg = y0 + ty;
+    const bool colok = xg < p.nx && yg < p.ny;
+    const int64_t colo = (int64_t)yg * p.pitch + xg;
+    float d2xy[4];
+    {
+        const float d2y = layer_d2(yg, p.phys_lo[1], p.phys_hi[1]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d2xy[j] = layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2y;
+    }
+    int ki = p.inj_ptr ? p.inj_ptr[tile] : 0, kie = p.inj_ptr ? p.inj_ptr[tile + 1] : 0;
+    int ks = p.smp_ptr ? p.smp_ptr[tile] : 0, kse = p.smp_ptr ? p.smp_ptr[tile + 1] : 0;
+    const int cA = (M + ty) * PW + HX + 4 * tx;        // my centre in the halo plane
+    const int cT = ty * kTX3 + 4 * tx;                 // my element in a tile
+
+    float4 q[QL];
+#pragma unroll
+    for (int i = 0; i < QL; ++i) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int slot = 0;
+    uint32_t fph = 0;
+    bool ok = true;
+
+    // stream index s = -2M + QL*k + u  (s mod QL = (u + 1) mod QL); the queue slot
+    // of the plane fed at stream index s is (s + 2M) mod QL = u
+    for (int k0 = 0; k0 < S; k0 += QL) {
+#pragma unroll
+        for (int u = 0; u < QL; ++u) {
+            const int si = k0 + u;            // 0-based stream index
+            if (si >= S) break;
+            ok = ok && mbar_wait_bounded(&full[slot], fph);
+            if (!ok) break;
+            const float *P = sm + slot * SLOT;
+            q[u] = ld4(P + C::AEL + 2 * C::TEL + cT);      // plane zb + si - M
+            if (si >= 2 * M) {
+                const int z = zb + si - 2 * M;
+                // queue slot of plane z + d is (u - M + d) mod QL
+                float win[4 + 2 * HX];
+#pragma unroll
+                for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
+                    const float4 a = ld4(P + cA - HX + 4 * i);
+                    win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+                }
+                float lap[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float acc = p.w[0] * win[HX + j];
+#pragma unroll
+                    for (int m = 1; m <= M; ++m)
+                        acc = fmaf(p.w[m * kWDim], win[HX + j + m] + win[HX + j - m], acc);
+                    lap[j] = acc;
+                }
+#pragma unroll
+                for (int m = 1; m <= M; ++m) {
+                    const float4 a = ld4(P + cA + m * PW);
+                    const float4 b = ld4(P + cA - m * PW);
+                    const float4 c = q[(u - M + m + 2 * QL) % QL];
+                    const float4 d = q[(u - M - m + 2 * QL) % QL];
+                    const float wm = p.w[m];
+                    lap[0] = fmaf(wm, (a.x + b.x) + (c.x + d.x), lap[0]);
+                    lap[1] = fmaf(wm, (a.y + b.y) + (c.y + d.y), lap[1]);
+                    lap[2] = fmaf(wm, (a.z + b.z) + (c.z + d.z), lap[2]);
+                    lap[3] = fmaf(wm, (a.w + b.w) + (c.w + d.w), lap[3]);
+                }
+                const float4 upv = ld4(P + C::AEL + cT);
+                const float4 kpv = ld4(P + C::AEL + C::TEL + cT);
+                const float4 cv = q[(u - M + 2 * QL) % QL];
+                const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
+                const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+                const float uu[4] = {upv.x, upv.y, upv.z, upv.w};
+                const float kk[4] = {kpv.x, kpv.y, kpv.z, kpv.w};
+                float o[4], dv[4], g[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    g[j] = p.gcoef * (d2xy[j] + d2z);
+                    dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
+                }
+                // the slot has been read: release it to the producer
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                if (p.inj_ptr)
+                    plane_entries(p.inj, ki, kie, z, tx, ty, [&](int j, const PtEntry &en) {
+                        float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
+                        if (MODE == kModeAdjoint) a *= kk[j];
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj)
+                            if (jj == j) o[jj] += a;
+                    });
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+                if (p.smp_ptr)
+                    plane_entries(p.smp, ks, kse, z, tx, ty, [&](int j, const PtEntry &en) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj)
+                            if (jj == j) v = o[jj];
+                        v *= en.scale;
+                        if (MODE == kModeAdjoint) v /= kk[j];
+                        p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
+                    });
+                if (colok) {
+                    const int64_t off = (int64_t)z * p.plane + colo;
+                    const float4 un = make_float4(o[0], o[1], o[2], o[3]);
+                    *reinterpret_cast<float4 *>(p.u_prev + off) = un;
+                    if (MODE == kModeStoreD)
+                        *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+                    if (MODE == kModeAdjoint) {
+                        const float4 dd = ldg4(p.dseg_in + off);
+                        float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
+                        ga.x = fmaf(un.x, dd.x, ga.x); ga.y = fmaf(un.y, dd.y, ga.y);
+                        ga.z = fmaf(un.z, dd.z, ga.z); ga.w = fmaf(un.w, dd.w, ga.w);
+                        *reinterpret_cast<float4 *>(p.gacc + off) = ga;
+                    }
+                }
+            } else {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
+            if (++slot == NR) {
+                slot = 0;
+                fph ^= 1u;
+            }
+        }
+        if (!ok) break;
+    }
+    if (!ok) {
+        atomicOr(p.status, kStatusTimeout);
+        *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+    }
+}
+
+template <int M, int TY>
+KernelFn pick_cross(int mode)
+{
+    switch (mode) {
+    case kModeForward: return step3d_cross<M, kModeForward, TY>;
+    case kModeStoreD: return step3d_cross<M, kModeStoreD, TY>;
+    default: return step3d_cross<M, kModeAdjoint, TY>;
+    }
+}
+
 KernelFn lookup3(int shape, int M, int ty, int mode)
 {
+#define FDW_Q(MM, TT) \
+    if (shape == FD_CROSS && M == MM && ty == TT) return pick_cross<MM, TT>(mode);
+    FDW_Q(1, 16) FDW_Q(2, 16) FDW_Q(3, 16) FDW_Q(4, 16) FDW_Q(6, 8) FDW_Q(8, 8)
+#undef FDW_Q
 #define FDW_C(S, MM, TT) \
     if (shape == S && M == MM && ty == TT) return pick3<S, MM, TT>(mode);
-    FDW_C(FD_CROSS, 1, 16) FDW_C(FD_CROSS, 2, 16) FDW_C(FD_CROSS, 3, 16) FDW_C(FD_CROSS, 4, 16)
-    FDW_C(FD_CROSS, 6, 8) FDW_C(FD_CROSS, 8, 8)
     FDW_C(FD_RHOMBUS, 2, 16) FDW_C(FD_RHOMBUS, 3, 16) FDW_C(FD_RHOMBUS, 4, 16)
     FDW_C(FD_RHOMBUS, 6, 8) FDW_C(FD_RHOMBUS, 8, 8)
     FDW_C(FD_SQUARE, 2, 16) FDW_C(FD_SQUARE, 4, 16)
@@ -275,6 +524,14 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
     v->box[1] = ty + 2 * M;
     v->box[2] = 1;
     v->smem = (size_t)(2 * M + 1 + kPF) * ((v->box[0] * v->box[1] + 31) & ~31) * sizeof(float);
+    v->tbox[0] = kTX3;
+    v->tbox[1] = ty;
+    if (shape == FD_CROSS) {   // warp-specialised pipeline: one extra producer warp
+        const int HXc = round4(M);
+        const int A = ((kTX3 + 2 * HXc) * (ty + 2 * M) + 31) & ~31;
+        v->smem = (size_t)4 * (A + 3 * kTX3 * ty) * sizeof(float);
+        v->threads = 16 * ty + 32;
+    }
     (void)nx; (void)ny; (void)nz;
     return 0;
 }
