@@ -132,6 +132,62 @@ __device__ __forceinline__ float step_update(float u, float up, float k, float l
     return d;
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32x2 arithmetic (sm_100 family): one instruction for two lanes,
+// each lane rounded exactly like the scalar operation.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// float4 in shared memory as two packed pairs (x, y) and (z, w)
+__device__ __forceinline__ void ld4x2(const float *p, f32x2 &a, f32x2 &b)
+{
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
+    a = v.x;
+    b = v.y;
+}
+// Packed form of step_update (same rounding, lane by lane).
+__device__ __forceinline__ f32x2 step_update2(f32x2 u, f32x2 up, f32x2 k, f32x2 lap, f32x2 g,
+                                              f32x2 &o)
+{
+    const f32x2 d = mul2(k, lap);
+    o = add2(add2(add2(sub2(u, up), u), d), mul2(g, up));
+    return d;
+}
+
 __device__ __forceinline__ float4 ld4(const float *p)
 {
     return *reinterpret_cast<const float4 *>(p);

@@ -34,6 +34,32 @@ __device__ __forceinline__ void plane_entries(const PtEntry *tab, int &k, int ke
     }
 }
 
+// Out-of-line handlers for the (rare) planes that carry table entries, so the
+// unrolled plane loops stay small.  Return the z of the next pending entry.
+template <int MODE>
+__device__ __noinline__ int inject_plane(const StepParams &p, int &k, int kend, int z, int tx,
+                                         int ty, float4 &o, const float4 &kk)
+{
+    plane_entries(p.inj, k, kend, z, tx, ty, [&](int j, const PtEntry &en) {
+        float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
+        if (MODE == kModeAdjoint) a *= get4(kk, j);
+        add4(o, j, a);
+    });
+    return k < kend ? p.inj[k].z : 0x7fffffff;
+}
+
+template <int MODE>
+__device__ __noinline__ int sample_plane(const StepParams &p, int &k, int kend, int z, int tx,
+                                         int ty, const float4 &o, const float4 &kk)
+{
+    plane_entries(p.smp, k, kend, z, tx, ty, [&](int j, const PtEntry &en) {
+        float v = get4(o, j) * en.scale;
+        if (MODE == kModeAdjoint) v /= get4(kk, j);
+        p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
+    });
+    return k < kend ? p.smp[k].z : 0x7fffffff;
+}
+
 template <int SHAPE, int M, int MODE, int TY>
 __global__ void __launch_bounds__(16 * TY) step3d_kernel(const __grid_constant__ StepParams p)
 {
@@ -270,7 +296,6 @@ struct CrossCfg {
     static constexpr int NR = 4;                          // ring depth
     static constexpr int NCW = TY / 2;                    // consumer warps
     static constexpr int THREADS = 16 * TY + 32;
-    static constexpr size_t SMEM = (size_t)NR * SLOT * sizeof(float);
 };
 
 template <int M, int MODE, int TY>
@@ -361,18 +386,20 @@ step3d_cross(const __grid_constant__ StepParams p)
     }
     int ki = p.inj_ptr ? p.inj_ptr[tile] : 0, kie = p.inj_ptr ? p.inj_ptr[tile + 1] : 0;
     int ks = p.smp_ptr ? p.smp_ptr[tile] : 0, kse = p.smp_ptr ? p.smp_ptr[tile + 1] : 0;
+    int zinj = ki < kie ? p.inj[ki].z : 0x7fffffff;    // z of the next table entry
+    int zsmp = ks < kse ? p.smp[ks].z : 0x7fffffff;
     const int cA = (M + ty) * PW + HX + 4 * tx;        // my centre in the halo plane
     const int cT = ty * kTX3 + 4 * tx;                 // my element in a tile
 
-    float4 q[QL];
+    // queue of centre values as packed pairs (x, y) and (z, w)
+    f32x2 qa[QL], qb[QL];
 #pragma unroll
-    for (int i = 0; i < QL; ++i) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < QL; ++i) qa[i] = qb[i] = 0ull;
     int slot = 0;
     uint32_t fph = 0;
     bool ok = true;
 
-    // stream index s = -2M + QL*k + u  (s mod QL = (u + 1) mod QL); the queue slot
-    // of the plane fed at stream index s is (s + 2M) mod QL = u
+    // stream index s = -2M + QL*k + u; the queue slot of the plane fed at s is u
     for (int k0 = 0; k0 < S; k0 += QL) {
 #pragma unroll
         for (int u = 0; u < QL; ++u) {
@@ -381,7 +408,7 @@ step3d_cross(const __grid_constant__ StepParams p)
             ok = ok && mbar_wait_bounded(&full[slot], fph);
             if (!ok) break;
             const float *P = sm + slot * SLOT;
-            q[u] = ld4(P + C::AEL + 2 * C::TEL + cT);      // plane zb + si - M
+            ld4x2(P + C::AEL + 2 * C::TEL + cT, qa[u], qb[u]);   // plane zb + si - M
             if (si >= 2 * M) {
                 const int z = zb + si - 2 * M;
                 // queue slot of plane z + d is (u - M + d) mod QL
@@ -391,30 +418,276 @@ step3d_cross(const __grid_constant__ StepParams p)
                     const float4 a = ld4(P + cA - HX + 4 * i);
                     win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
                 }
-                float lap[4];
+                float lx[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     float acc = p.w[0] * win[HX + j];
 #pragma unroll
                     for (int m = 1; m <= M; ++m)
                         acc = fmaf(p.w[m * kWDim], win[HX + j + m] + win[HX + j - m], acc);
-                    lap[j] = acc;
+                    lx[j] = acc;
                 }
+                f32x2 l01 = pk2(lx[0], lx[1]), l23 = pk2(lx[2], lx[3]);
+                // y and z arms: W[0][m] (u(y+m) + u(y-m) + u(z+m) + u(z-m)), two lanes per op
 #pragma unroll
                 for (int m = 1; m <= M; ++m) {
-                    const float4 a = ld4(P + cA + m * PW);
-                    const float4 b = ld4(P + cA - m * PW);
-                    const float4 c = q[(u - M + m + 2 * QL) % QL];
-                    const float4 d = q[(u - M - m + 2 * QL) % QL];
-                    const float wm = p.w[m];
-                    lap[0] = fmaf(wm, (a.x + b.x) + (c.x + d.x), lap[0]);
-                    lap[1] = fmaf(wm, (a.y + b.y) + (c.y + d.y), lap[1]);
-                    lap[2] = fmaf(wm, (a.z + b.z) + (c.z + d.z), lap[2]);
-                    lap[3] = fmaf(wm, (a.w + b.w) + (c.w + d.w), lap[3]);
+                    f32x2 a01, a23, b01, b23;
+                    ld4x2(P + cA + m * PW, a01, a23);
+                    ld4x2(P + cA - m * PW, b01, b23);
+                    const int ip = (u - M + m + 2 * QL) % QL, im = (u - M - m + 2 * QL) % QL;
+                    const f32x2 wm = pk2(p.w[m], p.w[m]);
+                    l01 = fma2(wm, add2(add2(a01, b01), add2(qa[ip], qa[im])), l01);
+                    l23 = fma2(wm, add2(add2(a23, b23), add2(qb[ip], qb[im])), l23);
                 }
-                const float4 upv = ld4(P + C::AEL + cT);
-                const float4 kpv = ld4(P + C::AEL + C::TEL + cT);
-                const float4 cv = q[(u - M + 2 * QL) % QL];
+                f32x2 up01, up23, k01, k23;
+                ld4x2(P + C::AEL + cT, up01, up23);
+                ld4x2(P + C::AEL + C::TEL + cT, k01, k23);
+                // the slot has been read: release it to the producer
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                const int ic = (u - M + 2 * QL) % QL;
+                const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
+                float g[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) g[j] = p.gcoef * (d2xy[j] + d2z);
+                f32x2 o01, o23;
+                const f32x2 dv01 = step_update2(qa[ic], up01, k01, l01, pk2(g[0], g[1]), o01);
+                const f32x2 dv23 = step_update2(qb[ic], up23, k23, l23, pk2(g[2], g[3]), o23);
+                float4 o, kk;
+                upk2(o01, o.x, o.y);
+                upk2(o23, o.z, o.w);
+                upk2(k01, kk.x, kk.y);
+                upk2(k23, kk.z, kk.w);
+                if (z >= zinj) zinj = inject_plane<MODE>(p, ki, kie, z, tx, ty, o, kk);
+                if (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f || g[3] != 0.f) {
+                    o.x = g[0] != 0.f ? __fdividef(o.x, 1.f + g[0]) : o.x;
+                    o.y = g[1] != 0.f ? __fdividef(o.y, 1.f + g[1]) : o.y;
+                    o.z = g[2] != 0.f ? __fdividef(o.z, 1.f + g[2]) : o.z;
+                    o.w = g[3] != 0.f ? __fdividef(o.w, 1.f + g[3]) : o.w;
+                }
+                if (z >= zsmp) zsmp = sample_plane<MODE>(p, ks, kse, z, tx, ty, o, kk);
+                if (colok) {
+                    const int64_t off = (int64_t)z * p.plane + colo;
+                    *reinterpret_cast<float4 *>(p.u_prev + off) = o;
+                    if (MODE == kModeStoreD)
+                        *reinterpret_cast<ulonglong2 *>(p.dseg_out + off) = make_ulonglong2(dv01, dv23);
+                    if (MODE == kModeAdjoint) {
+                        const float4 dd = ldg4(p.dseg_in + off);
+                        float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
+                        ga.x = fmaf(o.x, dd.x, ga.x); ga.y = fmaf(o.y, dd.y, ga.y);
+                        ga.z = fmaf(o.z, dd.z, ga.z); ga.w = fmaf(o.w, dd.w, ga.w);
+                        *reinterpret_cast<float4 *>(p.gacc + off) = ga;
+                    }
+                }
+            } else {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            }
+            if (++slot == NR) {
+                slot = 0;
+                fph ^= 1u;
+            }
+        }
+        if (!ok) break;
+    }
+    if (!ok) {
+        atomicOr(p.status, kStatusTimeout);
+        *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+    }
+}
+
+template <int M, int TY>
+struct PlanarCfg {
+    static constexpr int HX = round4(M);
+    static constexpr int PW = kTX3 + 2 * HX;
+    static constexpr int PH = TY + 2 * M;
+    static constexpr int AEL = (PW * PH + 31) & ~31;
+    static constexpr int TEL = kTX3 * TY;
+    static constexpr int SLOT = AEL + 3 * TEL;            // A | u_cur(P-M) | u_prev | kappa
+    static constexpr int NR = 4;
+    static constexpr int NCW = TY / 2;
+    static constexpr int THREADS = 16 * TY + 32;
+};
+
+template <int SHAPE, int M, int MODE, int TY>
+__global__ void __launch_bounds__(PlanarCfg<M, TY>::THREADS, TY == 16 ? 2 : 3)
+step3d_planar(const __grid_constant__ StepParams p)
+{
+    using C = PlanarCfg<M, TY>;
+    constexpr int HX = C::HX, PW = C::PW, PH = C::PH;
+    constexpr int NR = C::NR, SLOT = C::SLOT;
+    constexpr int QL = 2 * M + 1;
+    constexpr uint32_t BYTES_FULL = (PW * PH + 3 * C::TEL) * 4;
+    constexpr uint32_t BYTES_A = PW * PH * 4;
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t full[NR], empty[NR];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int ntile = p.tiles_x * p.tiles_y;
+    const int tile = blockIdx.x % ntile, zc = blockIdx.x / ntile;
+    const int x0 = (tile % p.tiles_x) * kTX3, y0 = (tile / p.tiles_x) * TY;
+    const int zb = zc * p.zchunk;
+    const int nz = (int)p.nz;
+    const int ze = min(nz, zb + p.zchunk);
+    const int L = ze - zb;
+    const int S = L + 2 * M;          // planes zb-M .. ze+M-1
+
+    if (tid == 0) {
+        for (int i = 0; i < NR; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], C::NCW);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == C::NCW) {
+        if (lane != 0) return;
+        prefetch_tmap(p.tmap);
+        prefetch_tmap(p.tmap_cur_t);
+        prefetch_tmap(p.tmap_prev_t);
+        prefetch_tmap(p.tmap_kappa_t);
+        volatile int *abort_v = &abort_flag;
+        int slot = 0, t = 0;
+        for (; t < S; ++t) {
+            if (t >= NR && !mbar_wait_bounded(&empty[slot], (uint32_t)((t / NR - 1) & 1))) {
+                atomicOr(p.status, kStatusTimeout);
+                *abort_v = 1;
+                break;
+            }
+            if (*abort_v) break;
+            float *dst = sm + slot * SLOT;
+            const int P = zb - M + t;
+            if (t < 2 * M) {
+                mbar_arrive_expect_tx(&full[slot], BYTES_A);
+            } else {
+                const int z = P - M;
+                mbar_arrive_expect_tx(&full[slot], BYTES_FULL);
+                tma_load_3d(dst + C::AEL, p.tmap_cur_t, &full[slot], x0, y0, z);
+                tma_load_3d(dst + C::AEL + C::TEL, p.tmap_prev_t, &full[slot], x0, y0, z);
+                tma_load_3d(dst + C::AEL + 2 * C::TEL, p.tmap_kappa_t, &full[slot], x0, y0, z);
+            }
+            tma_load_3d(dst, p.tmap, &full[slot], x0 - HX, y0 - M, P);
+            if (++slot == NR) slot = 0;
+        }
+        if (*abort_v) {
+            for (int i = max(0, t - NR); i < t; ++i)
+                mbar_wait_bounded(&full[i % NR], (i / NR) & 1, 100000000LL);
+        }
+        return;
+    }
+
+    const int ty = tid >> 4, tx = tid & 15;
+    const int xg = x0 + 4 * tx, yg = y0 + ty;
+    const bool colok = xg < p.nx && yg < p.ny;
+    const int64_t colo = (int64_t)yg * p.pitch + xg;
+    float d2xy[4];
+    {
+        const float d2y = layer_d2(yg, p.phys_lo[1], p.phys_hi[1]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d2xy[j] = layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2y;
+    }
+    int ki = p.inj_ptr ? p.inj_ptr[tile] : 0, kie = p.inj_ptr ? p.inj_ptr[tile + 1] : 0;
+    int ks = p.smp_ptr ? p.smp_ptr[tile] : 0, kse = p.smp_ptr ? p.smp_ptr[tile + 1] : 0;
+    const int cA = (M + ty) * PW + HX + 4 * tx;
+    const int cT = ty * kTX3 + 4 * tx;
+
+    float4 acc[QL];
+#pragma unroll
+    for (int i = 0; i < QL; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int slot = 0;
+    uint32_t fph = 0;
+    bool ok = true;
+
+    // output o accumulates in slot (o - zb + M) mod QL; at stream index t (plane
+    // P = zb - M + t, t = t0 + u with t0 a multiple of QL) output P + s is slot (u + s) mod QL
+    for (int t0 = 0; t0 < S; t0 += QL) {
+#pragma unroll
+        for (int u = 0; u < QL; ++u) {
+            const int t = t0 + u;
+            if (t >= S) break;
+            ok = ok && mbar_wait_bounded(&full[slot], fph);
+            if (!ok) break;
+            const float *A = sm + slot * SLOT;
+            acc[(u + M) % QL] = make_float4(0.f, 0.f, 0.f, 0.f);   // output P + M starts here
+            float T[M + 1][4];
+#pragma unroll
+            for (int s = 0; s <= M; ++s)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) T[s][j] = 0.f;
+            {   // row y of P: centre, in-plane x line (s = 0) and xz lines (s >= 1)
+                float win[4 + 2 * HX];
+#pragma unroll
+                for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
+                    const float4 a = ld4(A + cA - HX + 4 * i);
+                    win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float ps[M + 1];
+#pragma unroll
+                    for (int pp = 1; pp <= M; ++pp) ps[pp] = win[HX + j + pp] + win[HX + j - pp];
+#pragma unroll
+                    for (int s = 0; s <= M; ++s) {
+                        const int E = shape_ext(SHAPE, M, 0, s);
+                        float a = p.w[s] * win[HX + j];
+#pragma unroll
+                        for (int pp = 1; pp <= E; ++pp) a = fmaf(p.w[pp * kWDim + s], ps[pp], a);
+                        T[s][j] += a;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 1; q <= M; ++q) {   // row pairs y +- q: in-plane rows and yz columns
+                const int E = shape_ext(SHAPE, M, 0, q);
+                const int E4 = round4(E);
+                float win[4 + 2 * HX];
+                const float *rp = A + cA + q * PW - E4;
+                const float *rm = A + cA - q * PW - E4;
+#pragma unroll
+                for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
+                    float4 a = ld4(rp + 4 * i);
+                    const float4 b = ld4(rm + 4 * i);
+                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                    win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float a = p.w[q] * win[E4 + j];
+#pragma unroll
+                    for (int pp = 1; pp <= E; ++pp)
+                        a = fmaf(p.w[pp * kWDim + q], win[E4 + j + pp] + win[E4 + j - pp], a);
+                    T[0][j] += a;
+#pragma unroll
+                    for (int s = 1; s <= M; ++s)
+                        if (q <= shape_ext(SHAPE, M, 0, s)) T[s][j] = fmaf(p.w[q * kWDim + s], win[E4 + j], T[s][j]);
+                }
+            }
+            float4 cv = make_float4(0.f, 0.f, 0.f, 0.f), upv = cv, kpv = cv;
+            const bool fin = t >= 2 * M;
+            if (fin) {
+                cv = ld4(A + C::AEL + cT);
+                upv = ld4(A + C::AEL + C::TEL + cT);
+                kpv = ld4(A + C::AEL + 2 * C::TEL + cT);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            // scatter: T[0] -> output P, T[s] -> outputs P - s and P + s
+            acc[u].x += T[0][0]; acc[u].y += T[0][1]; acc[u].z += T[0][2]; acc[u].w += T[0][3];
+#pragma unroll
+            for (int s = 1; s <= M; ++s) {
+                float4 &ap = acc[(u + s) % QL];
+                float4 &am = acc[(u - s + QL) % QL];
+                ap.x += T[s][0]; ap.y += T[s][1]; ap.z += T[s][2]; ap.w += T[s][3];
+                am.x += T[s][0]; am.y += T[s][1]; am.z += T[s][2]; am.w += T[s][3];
+            }
+            if (fin) {   // output z = P - M is complete
+                const int z = zb + t - 2 * M;
+                const float4 lv = acc[(u - M + QL) % QL];
+                const float lap[4] = {lv.x, lv.y, lv.z, lv.w};
                 const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
                 const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
                 const float uu[4] = {upv.x, upv.y, upv.z, upv.w};
@@ -425,9 +698,6 @@ step3d_cross(const __grid_constant__ StepParams p)
                     g[j] = p.gcoef * (d2xy[j] + d2z);
                     dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
                 }
-                // the slot has been read: release it to the producer
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);
                 if (p.inj_ptr)
                     plane_entries(p.inj, ki, kie, z, tx, ty, [&](int j, const PtEntry &en) {
                         float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
@@ -463,9 +733,6 @@ step3d_cross(const __grid_constant__ StepParams p)
                         *reinterpret_cast<float4 *>(p.gacc + off) = ga;
                     }
                 }
-            } else {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);
             }
             if (++slot == NR) {
                 slot = 0;
@@ -477,6 +744,16 @@ step3d_cross(const __grid_constant__ StepParams p)
     if (!ok) {
         atomicOr(p.status, kStatusTimeout);
         *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+    }
+}
+
+template <int SHAPE, int M, int TY>
+KernelFn pick_planar(int mode)
+{
+    switch (mode) {
+    case kModeForward: return step3d_planar<SHAPE, M, kModeForward, TY>;
+    case kModeStoreD: return step3d_planar<SHAPE, M, kModeStoreD, TY>;
+    default: return step3d_planar<SHAPE, M, kModeAdjoint, TY>;
     }
 }
 
@@ -496,6 +773,12 @@ KernelFn lookup3(int shape, int M, int ty, int mode)
     if (shape == FD_CROSS && M == MM && ty == TT) return pick_cross<MM, TT>(mode);
     FDW_Q(1, 16) FDW_Q(2, 16) FDW_Q(3, 16) FDW_Q(4, 16) FDW_Q(6, 8) FDW_Q(8, 8)
 #undef FDW_Q
+#define FDW_P(S, MM, TT) \
+    if (shape == S && M == MM && ty == TT) return pick_planar<S, MM, TT>(mode);
+    FDW_P(FD_RHOMBUS, 2, 16) FDW_P(FD_RHOMBUS, 3, 16) FDW_P(FD_RHOMBUS, 4, 16)
+    FDW_P(FD_RHOMBUS, 6, 8) FDW_P(FD_RHOMBUS, 8, 8) FDW_P(FD_SQUARE, 2, 16) FDW_P(FD_SQUARE, 4, 16)
+#undef FDW_P
+    return nullptr;
 #define FDW_C(S, MM, TT) \
     if (shape == S && M == MM && ty == TT) return pick3<S, MM, TT>(mode);
     FDW_C(FD_RHOMBUS, 2, 16) FDW_C(FD_RHOMBUS, 3, 16) FDW_C(FD_RHOMBUS, 4, 16)
@@ -526,7 +809,7 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
     v->smem = (size_t)(2 * M + 1 + kPF) * ((v->box[0] * v->box[1] + 31) & ~31) * sizeof(float);
     v->tbox[0] = kTX3;
     v->tbox[1] = ty;
-    if (shape == FD_CROSS) {   // warp-specialised pipeline: one extra producer warp
+    {   // warp-specialised pipelines (cross and planar): one extra producer warp
         const int HXc = round4(M);
         const int A = ((kTX3 + 2 * HXc) * (ty + 2 * M) + 31) & ~31;
         v->smem = (size_t)4 * (A + 3 * kTX3 * ty) * sizeof(float);

@@ -1,0 +1,89 @@
+"""Shot-parallel execution across ranks.
+
+Shots are independent forward problems and independent terms of the FWI
+misfit J = sum_s 1/2 ||d_s - d_obs,s||^2, so ranks split the shot list and the
+only exchange is one sum of (J, dJ/dm) at the end (torch.distributed
+all-reduce: NCCL between GPUs, gloo on CPU).  The per-shot work is a callable,
+so the same host logic drives the CUDA path (``gpu_shot_fn``) and, in tests,
+CPU stand-ins on gloo ranks.
+"""
+from __future__ import annotations
+
+from typing import Callable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+def shard(nshots: int, rank: int, world: int) -> List[int]:
+    """Contiguous, balanced block of shot indices for `rank` (sizes differ by
+    at most one; ranks beyond nshots get none)."""
+    if world < 1 or not (0 <= rank < world):
+        raise ValueError("bad rank/world %d/%d" % (rank, world))
+    base, extra = divmod(nshots, world)
+    lo = rank * base + min(rank, extra)
+    hi = lo + base + (1 if rank < extra else 0)
+    return list(range(lo, hi))
+
+
+def _dist():
+    try:
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            return dist
+    except Exception:
+        pass
+    return None
+
+
+def misfit_and_gradient(template, nshots: int,
+                        per_shot: Callable[[int], Tuple[float, "object"]],
+                        rank: Optional[int] = None, world: Optional[int] = None):
+    """Sum (J_s, g_s) over this rank's shots, then all-reduce the sums over
+    ranks.  ``per_shot(s)`` returns (J_s, g_s) with g_s a tensor shaped like
+    `template` (which fixes shape, dtype and device, so that ranks without
+    shots contribute zeros).  Returns (J, g), identical on every rank."""
+    import torch
+    dist = _dist()
+    if rank is None or world is None:
+        rank, world = (dist.get_rank(), dist.get_world_size()) if dist else (0, 1)
+    g = torch.zeros_like(template)
+    J = 0.0
+    for s in shard(nshots, rank, world):
+        Js, gs = per_shot(s)
+        J += float(Js)
+        g.add_(gs)
+    if dist is not None and world > 1:
+        Jt = torch.tensor([J], dtype=g.dtype, device=g.device)
+        dist.all_reduce(Jt)
+        dist.all_reduce(g)
+        J = float(Jt.item())
+    return J, g
+
+
+def gpu_shot_fn(plan, model_m, src_idx: Sequence[np.ndarray], wavelets, rec_idx: np.ndarray,
+                d_obs, k: int = 20):
+    """Per-shot (J_s, dJ/dm) on the GPU for m = 1/v^2: forward traces, residual
+    d - d_obs, adjoint gradient with checkpoints every k steps."""
+    import torch
+    from . import (FD_MODEL_SLOWNESS2, fd_adjoint_gradient, fd_forward, fd_status_read,
+                   workspace)
+    dev = model_m.device
+    nrec = len(rec_idx)
+    wsf = workspace(plan.forward_workspace_size(1, nrec), dev)
+    wsg = workspace(plan.gradient_workspace_size(1, nrec, k), dev)
+
+    def run(s):
+        tr = torch.empty((plan.nt, nrec), device=dev)
+        fd_forward(plan, model_m, src_idx[s], wavelets[s], rec_idx, tr, wsf,
+                   model_kind=FD_MODEL_SLOWNESS2)
+        r = tr - d_obs[s]
+        J = 0.5 * float((r.double() ** 2).sum())
+        g = torch.empty_like(model_m)
+        fd_adjoint_gradient(plan, model_m, src_idx[s], wavelets[s], rec_idx, r, k, g, wsg,
+                            model_kind=FD_MODEL_SLOWNESS2)
+        rc = fd_status_read(plan, wsg)
+        if rc != 0:
+            raise RuntimeError("device status %d in shot %d" % (rc, s))
+        return J, g
+
+    return run
