@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=400, help="physical nodes per axis")
     ap.add_argument("--nt", type=int, default=1500)
+    ap.add_argument("--workload", default="3d", choices=["3d", "2d", "batched", "fwi"],
+                    help="3d: 400^3 forward (default); 2d: 1001^2 x 18 stencils; batched: "
+                         "48 2D shots on three grids; fwi: 256^3 gradient, 16 shots")
+    ap.add_argument("--shots", type=int, default=0, help="fwi/batched: use the first N shots")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -261,6 +265,176 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_other(args):
+    """2D, batched and FWI-gradient workloads (same JSON contract)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2606_04882_gb300 as F
+    import workloads as WL
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    jobs = []          # (name, enqueue(nt0: bool), points, nt, launches per run)
+    h2d = d2h = 0
+    if args.workload == "2d":
+        pr = WL.layered_random_2d()
+        vel = torch.from_numpy(pr.vel).to(dev)
+        for st in pr.stencils:
+            pw_dt = 0.5 * F.fd_cfl_limit(F.stencil_desc(2, "cross", st.M)) * pr.h / pr.vmax
+            desc = F.stencil_desc(2, st.shape, st.M, 0, st.scheme, courant=pr.vmax * pw_dt / pr.h)
+            plan = F.Plan(pr.shape, pr.h, pw_dt, pr.nt, pr.nb, pr.vmax, desc)
+            plan0 = F.Plan(pr.shape, pr.h, pw_dt, 0, pr.nb, pr.vmax, desc)
+            si, ri = plan.linear_index(pr.src), plan.linear_index(pr.rec)
+            wav = torch.from_numpy(F.fd_ricker(pr.f0, pw_dt, pr.nt)[:, None].copy()).to(dev)
+            tr = torch.empty((pr.nt, len(ri)), device=dev)
+            ws = F.workspace(plan.forward_workspace_size(1, len(ri)), dev)
+            inf = plan.info()
+            pts = int(inf.padded[0] * inf.padded[2])
+
+            def enq(zero, plan=plan, plan0=plan0, si=si, ri=ri, wav=wav, tr=tr, ws=ws):
+                F.fd_forward(plan0 if zero else plan, vel, si, wav, ri, tr, ws)
+            jobs.append(("%s%d_%s" % (st.shape, st.M, st.scheme), enq, pts, pr.nt, pr.nt + 1))
+            d2h += tr.numel() * 4
+        h2d = vel.numel() * 4
+        wl = "2d_layered_random_1001 (1081^2 padded), 2000 steps, 18 stencils"
+    elif args.workload == "batched":
+        probs = WL.batched_shots_2d()
+        if args.shots:
+            probs = probs[:args.shots]
+        dt = min(0.5 * F.fd_cfl_limit(F.stencil_desc(2, "cross", 4)) * p.h / p.vmax for p in probs)
+        nt = probs[0].nt
+
+        def make(nt_):
+            shots, keep = [], []
+            for pr in probs:
+                plan = F.Plan(pr.shape, pr.h, dt, nt_, pr.nb, pr.vmax, F.stencil_desc(2, "cross", 4))
+                shots.append(dict(plan=plan, model=torch.from_numpy(pr.vel).to(dev),
+                                  src_idx=plan.linear_index(pr.src),
+                                  wavelet=torch.from_numpy(F.fd_ricker(pr.f0, dt, nt)[:, None].copy()).to(dev),
+                                  rec_idx=plan.linear_index(pr.rec),
+                                  traces=torch.empty((nt, len(pr.rec)), device=dev)))
+            return shots
+        shots, shots0 = make(nt), make(0)
+        ws = F.workspace(max(F.batched_workspace_size(shots), F.batched_workspace_size(shots0)), dev)
+        pts = 0
+        for d in shots:
+            inf = d["plan"].info()
+            pts += int(inf.padded[0] * inf.padded[2])
+
+        def enq(zero):
+            F.fd_forward_batched(shots0 if zero else shots, ws)
+        jobs.append(("batched_cross4_%dshots" % len(probs), enq, pts, nt, nt + len(probs)))
+        h2d = sum(d["model"].numel() * 4 for d in shots)
+        d2h = sum(d["traces"].numel() * 4 for d in shots)
+        wl = "2d_batched %d shots on 1201x601/801x401/2001x801 (+20 sponge), 3000 steps, cross4" % len(probs)
+    else:   # fwi
+        probs, true = WL.fwi_3d()
+        if args.shots:
+            probs = probs[:args.shots]
+        pr0 = probs[0]
+        dt = 0.5 * F.fd_cfl_limit(F.stencil_desc(3, "cross", 4)) * pr0.h / pr0.vmax
+        plan = F.Plan(pr0.shape, pr0.h, dt, pr0.nt, pr0.nb, pr0.vmax, F.stencil_desc(3, "cross", 4))
+        m = torch.from_numpy((1.0 / pr0.vel.astype(np.float64) ** 2).astype(np.float32)).to(dev)
+        ri = plan.linear_index(pr0.rec)
+        wav = torch.from_numpy(F.fd_ricker(pr0.f0, dt, pr0.nt)[:, None].copy()).to(dev)
+        resid = torch.randn((pr0.nt, len(ri)), device=dev, generator=torch.Generator(dev).manual_seed(5))
+        grad = torch.empty_like(m)
+        k = 20
+        ws = F.workspace(plan.gradient_workspace_size(1, len(ri), k), dev)
+        inf = plan.info()
+        pts = int(inf.padded[0] * inf.padded[1] * inf.padded[2])
+        for i, pr in enumerate(probs):
+            si = plan.linear_index(pr.src)
+
+            def enq(zero, si=si):
+                if zero:
+                    return
+                F.fd_adjoint_gradient(plan, m, si, wav, ri, resid, k, grad, ws,
+                                      model_kind=F.FD_MODEL_SLOWNESS2)
+            jobs.append(("gradient_shot%d" % i, enq, pts, pr0.nt, 3 * pr0.nt + 1))
+        h2d = m.numel() * 4
+        d2h = m.numel() * 4
+        wl = "3d_fwi_256 (296^3 padded), %d shots, 1200 steps, cross4, checkpoints every 20" % len(probs)
+
+    def step(ev=None):
+        for i, (_, enq, _, _, _) in enumerate(jobs):
+            if ev is not None:
+                ev[i][0].record(stream)
+            enq(False)
+            if ev is not None:
+                ev[i][1].record(stream)
+
+    setup_ms = []
+    for (_, enq, _, _, _) in jobs:
+        enq(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        enq(True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        setup_ms.append(a.elapsed_time(b))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in jobs] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for kk in range(args.steps):
+        step(ev[kk])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    work = sum(j[2] * j[3] for j in jobs) * args.steps * world
+    value = work / (ms * 1e-3) / 1e9
+    peak, peak_kind = load_peaks()
+    kernels = []
+    bpp = 16.0 if args.workload != "fwi" else 16.0 * 3 + 8.0 / 20 + 4 + 4 + 8
+    for i, (name, _, pts, nt, _) in enumerate(jobs):
+        run_ms = statistics.mean(ev[kk][i][0].elapsed_time(ev[kk][i][1]) for kk in range(args.steps))
+        per = max(run_ms - setup_ms[i], 1e-9) / nt
+        gbs = bpp * pts / (per * 1e-3) / 1e9
+        kernels.append({"run": name, "ms_per_time_step": per, "achieved_gbs": gbs, "frac": gbs / peak,
+                        "gpts": pts / (per * 1e-3) / 1e9, "run_ms": run_ms})
+    dom = max(range(len(jobs)), key=lambda i: kernels[i]["run_ms"])
+    roof = {"bound": "hbm", "achieved": kernels[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": kernels[dom]["frac"], "traffic": None, "kernel": kernels[dom]["run"],
+            "bytes_per_point": bpp, "peak_source": peak_kind}
+    if args.workload == "2d":
+        roof["note"] = "fields (4.7 MB) are L2-resident: the HBM fraction is nominal"
+    if args.workload == "fwi":
+        roof["note"] = ("bytes per point per time step of the whole gradient: forward, recompute "
+                        "and adjoint sweeps (3 x 16) + checkpoints (8/k) + D store/load (8) + "
+                        "gradient accumulator (8)")
+    out = {"metric": "grid-point updates/s (%s)" % args.workload, "value": value, "unit": "Gpts/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": wl, "l2": "see roofline note" if args.workload == "2d" else "inputs larger than L2"},
+           "e2e": None, "roofline": roof, "kernels": kernels, "cpu_baseline": None,
+           "clocks": clocks,
+           "gpu_launches": args.steps * sum(j[4] for j in jobs)}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(pr, dt, steps=2):
     """The FP64 oracle on a bounded sample: `steps` time steps of the full
     460^3 grid with the Cross(4) stencil on all host cores."""
@@ -322,5 +496,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
-    else:
+    elif a.workload == "3d":
         run_gpu(a)
+    else:
+        run_other(a)

@@ -172,6 +172,20 @@ typedef struct {
 int fd_plan_get_info(const fd_plan *plan, fd_plan_info *info);
 
 /*
+ * fd_plan_autotune - pick the plan's kernel variant by measurement: each
+ * candidate tile shape (rows per thread in 2D; y tile and z-chunk length in
+ * 3D) runs 8 steps of this plan's problem on `model_d` with no sources or
+ * receivers, and the fastest is kept in the plan and in a per-process cache
+ * keyed by device name, dimension, shape, M, N and padded size (appended to
+ * the file named by the environment variable FDWAVE_TUNE_CACHE, and read
+ * from it, when that is set).  Synchronises `stream`.  Results of the plan's
+ * calls do not depend on the variant.  ws_d: >= fd_forward_workspace_size(plan,
+ * 0, 0) + 1 KiB.  Errors: FD_ERR_ARG, FD_ERR_NOMEM, FD_ERR_CUDA.
+ */
+int fd_plan_autotune(fd_plan *plan, int model_kind, const float *model_d, void *ws_d,
+                     size_t ws_bytes, void *stream);
+
+/*
  * fd_forward_workspace_size - bytes of device workspace fd_forward needs for
  * nsrc sources and nrec receivers (three padded field buffers, tile-bucketed
  * source/receiver tables, the status word).

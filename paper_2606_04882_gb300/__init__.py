@@ -79,6 +79,7 @@ _SIGS = {
     "fd_plan_create": (_I, [_P, _P, _P]),
     "fd_plan_destroy": (None, [_P]),
     "fd_plan_get_info": (_I, [_P, _P]),
+    "fd_plan_autotune": (_I, [_P, _I, _P, _P, _SZ, _P]),
     "fd_forward_workspace_size": (_I, [_P, _I, _I, _P]),
     "fd_forward": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
     "fd_status_read": (_I, [_P, _P, _P]),
@@ -213,6 +214,13 @@ class Plan:
         inf = self.info()
         p = tuple(inf.padded)
         return (p[0], p[2]) if self.dim == 2 else p
+
+    def autotune(self, model, model_kind: int = FD_MODEL_VELOCITY, stream=None):
+        """fd_plan_autotune on a scratch workspace (torch allocation)."""
+        ws = workspace(self.forward_workspace_size(0, 0) + 4096, model.device)
+        _check(lib().fd_plan_autotune(self.ptr, model_kind, _addr(model), _addr(ws), ws.numel(),
+                                      _stream_ptr(stream)))
+        return self.info()
 
     def forward_workspace_size(self, nsrc: int, nrec: int) -> int:
         b = ctypes.c_size_t(0)

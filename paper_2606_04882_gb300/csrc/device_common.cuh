@@ -114,10 +114,13 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 // ---------------------------------------------------------------------------
 // Damping: squared node distance into the sponge along one axis.
 // ---------------------------------------------------------------------------
+// (32-bit integer arithmetic: padded sizes are below 2^24 per axis, and a
+// 64-bit integer to float conversion would run on the FP64 pipe.)
 __device__ __forceinline__ float layer_d2(int64_t i, int64_t lo, int64_t hi)
 {
-    const int64_t d = i < lo ? lo - i : (i > hi ? i - hi : 0);
-    return static_cast<float>(d * d);
+    const int ii = (int)i, l = (int)lo, h = (int)hi;
+    const int d = ii < l ? l - ii : (ii > h ? ii - h : 0);
+    return __int2float_rn(d * d);
 }
 
 // Leapfrog bracket with explicit rounding (no contraction), so every kernel

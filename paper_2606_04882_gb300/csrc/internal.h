@@ -67,6 +67,33 @@ struct StepParams {
     float w[kWDim * kWDim];    // symmetric weight table W[p][q] = a_orbit(max, min)
 };
 
+// Batched 2D shots: per-shot descriptor in device memory (64-byte aligned for
+// the tensor maps) and the launch parameters of one time step.
+struct alignas(64) ShotDesc {
+    CUtensorMap tmap[2];       // halo-box maps of field buffers 0 and 1
+    float *buf[2];             // buffer 0 holds u^0 at the start, buffer 1 u^{-1}
+    const float *kappa;
+    const int32_t *inj_ptr;
+    const PtEntry *inj;
+    const float *inj_series;
+    const int32_t *smp_ptr;
+    const PtEntry *smp;
+    float *smp_out;
+    int64_t nx, nz, pitch;
+    int64_t phys_lo[3], phys_hi[3];
+    float gcoef;
+    int tiles_x, inj_ncol, smp_ncol;
+};
+
+struct BatchParams {
+    const ShotDesc *shots;
+    const int32_t *tile_shot;  // global tile -> shot
+    const int32_t *tile_local; // global tile -> tile within the shot
+    int step;                  // time step n (field parity and series row)
+    int *status;
+    float w[kWDim * kWDim];
+};
+
 // Kernel variant descriptor chosen by the plan.
 struct Variant {
     int dim, shape, M, N;
@@ -79,10 +106,16 @@ struct Variant {
 };
 
 // Host launchers (defined in the .cu files).
-int select_variant_2d(int shape, int M, int N, int64_t nx, int64_t nz, Variant *v);
-int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t nz, Variant *v);
+int select_variant_2d(int shape, int M, int N, int64_t nx, int64_t nz, Variant *v, int r_pref = 0);
+int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t nz, Variant *v,
+                      int ty_pref = 0);
+// Tuning candidates: rows per thread (2D) / y tile (3D) with a kernel.
+int variants_2d(int shape, int M, int *r_out, int cap);
+int variants_3d(int shape, int M, int *ty_out, int cap);
 cudaError_t launch_step2d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
 cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
+int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v);
+cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s);
 
 // aux kernels
 cudaError_t launch_prep_kappa(const float *model, int kind, float *kappa, int dim,

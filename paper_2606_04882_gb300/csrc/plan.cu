@@ -5,6 +5,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -77,14 +79,26 @@ struct Tables {
     bool has_adj = false;
 };
 
-size_t table_bytes(const fd_plan *p, int nsrc, int nrec, bool adj)
+// Tile geometry the point tables are built for.
+struct TileGeo {
+    int tx, tz, tiles_x, ntiles;
+};
+
+TileGeo plan_geo(const fd_plan *p) { return {p->var.tx, p->var.tz, p->tiles_x, p->ntiles}; }
+
+size_t table_bytes_n(int ntiles, int nsrc, int nrec, bool adj)
 {
-    const size_t ptr = up((p->ntiles + 1) * sizeof(int32_t));
+    const size_t ptr = up((ntiles + 1) * sizeof(int32_t));
     size_t b = 2 * ptr + up(std::max(nsrc, 1) * sizeof(PtEntry)) + up(std::max(nrec, 1) * sizeof(PtEntry));
     return adj ? 2 * b : b;
 }
 
-Layout make_layout(const fd_plan *p, int nsrc, int nrec, bool grad, int kseg)
+size_t table_bytes(const fd_plan *p, int nsrc, int nrec, bool adj)
+{
+    return table_bytes_n(p->ntiles, nsrc, nrec, adj);
+}
+
+Layout make_layout(const fd_plan *p, int nsrc, int nrec, bool grad, int kseg, int ntiles_tab = -1)
 {
     Layout L;
     const size_t fb = up(p->field * sizeof(float));
@@ -102,7 +116,8 @@ Layout make_layout(const fd_plan *p, int nsrc, int nrec, bool grad, int kseg)
         L.dseg = o; o += (size_t)kseg * fb;
     }
     L.tab = o;
-    L.tab_bytes = table_bytes(p, nsrc, nrec, grad);
+    L.tab_bytes = ntiles_tab >= 0 ? table_bytes_n(ntiles_tab, nsrc, nrec, grad)
+                                  : table_bytes(p, nsrc, nrec, grad);
     o += L.tab_bytes;
     L.total = o;
     return L;
@@ -114,70 +129,71 @@ struct Pt {
     PtEntry e;
 };
 
-int locate(const fd_plan *p, int64_t idx, int col, float scale, Pt &out)
+int locate(const fd_plan *p, const TileGeo &G, int64_t idx, int col, float scale, Pt &out)
 {
     const fd_problem &pr = p->prob;
     const int64_t nphys = pr.n[0] * pr.n[1] * pr.n[2];
     if (idx < 0 || idx >= nphys) return set_error(FD_ERR_ARG, "point index %lld outside the physical grid", (long long)idx);
     const int64_t ix = idx % pr.n[2], r = idx / pr.n[2], iy = r % pr.n[1], iz = r / pr.n[1];
     const int64_t x = ix + pr.nb, z = iz + pr.nb, y = pr.dim == 3 ? iy + pr.nb : 0;
-    const int tx = (int)(x / p->var.tx);
+    const int tx = (int)(x / G.tx);
     int tile;
     int64_t yl;
     if (pr.dim == 2) {
-        tile = (int)(z / p->var.tz) * p->tiles_x + tx;
+        tile = (int)(z / G.tz) * G.tiles_x + tx;
         yl = 0;
     } else {
-        tile = (int)(y / p->var.tz) * p->tiles_x + tx;
-        yl = y % p->var.tz;
+        tile = (int)(y / G.tz) * G.tiles_x + tx;
+        yl = y % G.tz;
     }
     out.tile = tile;
     out.e.z = (int32_t)z;
-    out.e.yx = (int32_t)((yl << 16) | (x % p->var.tx));
+    out.e.yx = (int32_t)((yl << 16) | (x % G.tx));
     out.e.col = col;
     out.e.scale = scale;
     return FD_OK;
 }
 
-int build_table(const fd_plan *p, int n, const int64_t *idx, float scale, std::vector<int32_t> &ptr,
-                std::vector<PtEntry> &ent)
+int build_table(const fd_plan *p, const TileGeo &G, int n, const int64_t *idx, float scale,
+                std::vector<int32_t> &ptr, std::vector<PtEntry> &ent)
 {
     std::vector<Pt> pts(n);
     for (int i = 0; i < n; ++i) {
-        int st = locate(p, idx[i], i, scale, pts[i]);
+        int st = locate(p, G, idx[i], i, scale, pts[i]);
         if (st) return st;
     }
     std::stable_sort(pts.begin(), pts.end(), [](const Pt &a, const Pt &b) {
         return a.tile != b.tile ? a.tile < b.tile : a.e.z < b.e.z;
     });
-    ptr.assign(p->ntiles + 1, 0);
+    ptr.assign(G.ntiles + 1, 0);
     for (auto &q : pts) ptr[q.tile + 1]++;
-    for (int t = 0; t < p->ntiles; ++t) ptr[t + 1] += ptr[t];
+    for (int t = 0; t < G.ntiles; ++t) ptr[t + 1] += ptr[t];
     ent.resize(pts.size());
     for (size_t i = 0; i < pts.size(); ++i) ent[i] = pts[i].e;
     return FD_OK;
 }
 
 int make_tables(const fd_plan *p, int nsrc, const int64_t *src, int nrec, const int64_t *rec,
-                bool adj, Tables &T)
+                bool adj, Tables &T, const TileGeo *geo = nullptr)
 {
+    const TileGeo G = geo ? *geo : plan_geo(p);
     const fd_problem &pr = p->prob;
     const double hd = std::pow(pr.h, pr.dim);
     const float src_scale = (float)(pr.dt * pr.dt / hd);
     std::vector<int32_t> a, b, c, d;
     std::vector<PtEntry> ea, eb, ec, ed;
     int st;
-    if ((st = build_table(p, nsrc, src, src_scale, a, ea))) return st;
-    if ((st = build_table(p, nrec, rec, 1.0f, b, eb))) return st;
+    if ((st = build_table(p, G, nsrc, src, src_scale, a, ea))) return st;
+    if ((st = build_table(p, G, nrec, rec, 1.0f, b, eb))) return st;
     if (adj) {
         // adjoint (q = s2 nu form): residual injected as kappa * h^2 * r (kappa applied
         // in the kernel); source samples give dJ/ds = q tau^2 / (h^dim h^2 kappa)
-        if ((st = build_table(p, nrec, rec, (float)(pr.h * pr.h), c, ec))) return st;
-        if ((st = build_table(p, nsrc, src, (float)(pr.dt * pr.dt / (hd * pr.h * pr.h)), d, ed))) return st;
+        if ((st = build_table(p, G, nrec, rec, (float)(pr.h * pr.h), c, ec))) return st;
+        if ((st = build_table(p, G, nsrc, src, (float)(pr.dt * pr.dt / (hd * pr.h * pr.h)), d, ed))) return st;
     }
-    const size_t ptrb = up((p->ntiles + 1) * sizeof(int32_t));
+    const size_t ptrb = up((G.ntiles + 1) * sizeof(int32_t));
     const size_t sb = up(std::max(nsrc, 1) * sizeof(PtEntry)), rb = up(std::max(nrec, 1) * sizeof(PtEntry));
-    T.blob.assign(table_bytes(p, nsrc, nrec, adj), 0);
+    T.blob.assign(table_bytes_n(G.ntiles, nsrc, nrec, adj), 0);
     size_t o = 0;
     auto put = [&](size_t &off, const void *src_, size_t bytes, size_t span) {
         off = o;
@@ -391,6 +407,161 @@ extern "C" int fd_plan_create(const fd_problem *prob, const fd_stencil_desc *ste
 }
 
 extern "C" void fd_plan_destroy(fd_plan *plan) { delete plan; }
+
+// ------------------------------- autotuner --------------------------------
+namespace {
+
+// Re-derive the tile counts of a plan for a kernel variant.
+void apply_variant(fd_plan *p, const Variant &v)
+{
+    p->var = v;
+    p->tiles_x = (int)((p->pad[2] + v.tx - 1) / v.tx);
+    p->tiles_y = (int)(((p->prob.dim == 2 ? p->pad[0] : p->pad[1]) + v.tz - 1) / v.tz);
+    p->ntiles = p->tiles_x * p->tiles_y;
+    p->tuned = false;
+}
+
+struct TuneChoice {
+    int pref;        // rows per thread (2D) or y tile (3D)
+    int zchunk;      // 3D z-chunk (0 in 2D)
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;
+
+std::string tune_key(const fd_plan *p)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%d|%lld|%lld|%lld", prop.name, p->prob.dim, p->shape_eff,
+             p->st.M, p->st.N, (long long)p->pad[0], (long long)p->pad[1], (long long)p->pad[2]);
+    for (char *c = buf; *c; ++c)
+        if (*c == ' ') *c = '_';
+    return buf;
+}
+
+void tune_file_load()
+{
+    static bool done = false;
+    const char *path = getenv("FDWAVE_TUNE_CACHE");
+    if (done || !path) return;
+    done = true;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int a, b;
+    while (fscanf(f, "%255s %d %d", key, &a, &b) == 3) g_tune[key] = {a, b};
+    fclose(f);
+}
+
+void tune_file_store(const std::string &key, const TuneChoice &c)
+{
+    const char *path = getenv("FDWAVE_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d\n", key.c_str(), c.pref, c.zchunk);
+    fclose(f);
+}
+
+int apply_choice(fd_plan *p, const TuneChoice &c)
+{
+    Variant v;
+    const int M = p->st.M;
+    int st = p->prob.dim == 2
+                 ? select_variant_2d(p->shape_eff, M, p->st.N, p->pad[2], p->pad[0], &v, c.pref)
+                 : select_variant_3d(p->shape_eff, M, p->st.N, p->pad[2], p->pad[1], p->pad[0], &v, c.pref);
+    if (st) return st;
+    apply_variant(p, v);
+    if (p->prob.dim == 3) {
+        p->zchunk = c.zchunk;
+        p->nz_chunks = (int)((p->pad[0] + c.zchunk - 1) / c.zchunk);
+        p->tuned = true;
+    } else {
+        p->tuned = true;
+    }
+    return FD_OK;
+}
+
+}  // namespace
+
+extern "C" int fd_plan_autotune(fd_plan *p, int model_kind, const float *model, void *ws,
+                                size_t ws_bytes, void *stream)
+{
+    clear_error();
+    if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
+    size_t need = make_layout(p, 0, 0, false, 1).total;
+    // variants with more tiles need larger tables: size for the worst case
+    need += 4 * kAlign;
+    int st = check_common(p, model_kind, model, 0, nullptr, nullptr, 0, nullptr, ws, ws_bytes, 0);
+    if (st) return st;
+    if (ws_bytes < need) return set_error(FD_ERR_NOMEM, "autotune workspace has %zu bytes, needs %zu", ws_bytes, need);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_file_load();
+    const std::string key = tune_key(p);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return apply_choice(p, it->second);
+    if (p->var.generic) return FD_OK;   // a single kernel: nothing to choose
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int prefs[4];
+    const int np = p->prob.dim == 2 ? variants_2d(p->shape_eff, p->st.M, prefs, 4)
+                                    : variants_3d(p->shape_eff, p->st.M, prefs, 4);
+    std::vector<TuneChoice> cands;
+    for (int i = 0; i < np; ++i) {
+        if (p->prob.dim == 2) {
+            cands.push_back({prefs[i], 0});
+            continue;
+        }
+        fd_plan q = *p;
+        if (apply_choice(&q, {prefs[i], (int)q.pad[0]})) continue;
+        q.tuned = false;
+        if ((st = ensure_tuned(&q))) return st;        // cost-model z-chunk for this tile
+        const int base = q.zchunk;
+        for (int f : {1, 2, 4}) {
+            const int zc = std::max(2 * p->st.M, base / f);
+            if (f > 1 && zc == cands.back().zchunk) continue;
+            cands.push_back({prefs[i], zc});
+        }
+        if (base * 2 <= q.pad[0]) cands.push_back({prefs[i], base * 2});
+    }
+    if (cands.empty()) return set_error(FD_ERR_UNSUPPORTED, "no kernel variant to tune");
+    cudaEvent_t e0, e1;
+    FDW_CK(cudaEventCreate(&e0));
+    FDW_CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    TuneChoice bestc = cands[0];
+    for (const TuneChoice &c : cands) {
+        fd_plan q = *p;
+        if (apply_choice(&q, c)) continue;
+        q.prob.nt = 8;
+        if (make_layout(&q, 0, 0, false, 1).total > ws_bytes) continue;
+        st = fd_forward(&q, model_kind, model, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr,
+                        nullptr, ws, ws_bytes, stream);
+        if (st) break;
+        FDW_CK(cudaEventRecord(e0, s));
+        for (int r = 0; r < 2; ++r)
+            st = st ? st : fd_forward(&q, model_kind, model, 0, nullptr, nullptr, 0, nullptr, nullptr,
+                                      nullptr, nullptr, ws, ws_bytes, stream);
+        FDW_CK(cudaEventRecord(e1, s));
+        FDW_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        FDW_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (st) break;
+        if (ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    g_tune[key] = bestc;
+    tune_file_store(key, bestc);
+    return apply_choice(p, bestc);
+}
 
 extern "C" int fd_plan_get_info(const fd_plan *p, fd_plan_info *info)
 {
@@ -677,19 +848,84 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
 }
 
 // ------------------------------ batched shots ------------------------------
-// Each shot gets its own slice of the workspace (forward layout); every time
-// step launches the step kernel of each shot in turn, and the whole time loop
-// is captured once into a CUDA graph and replayed.
+// 2D shots sharing a specialised stencil run as one launch per time step over
+// a tile table spanning every shot (step2d_batched); other batches launch the
+// step kernel of each shot in turn.  Either way the whole time loop is
+// captured once into a CUDA graph and replayed.
+
+namespace {
+
+// Common batch variant for 2D shots (nullptr if the batch needs per-shot launches).
+bool batch_geometry(int nshots, const fd_shot *shots, Variant &bv, std::vector<TileGeo> &geo)
+{
+    const fd_plan *p0 = shots[0].plan;
+    if (p0->prob.dim != 2 || p0->var.generic) return false;
+    int64_t tiles4 = 0;
+    for (int i = 0; i < nshots; ++i) {
+        const fd_plan *q = shots[i].plan;
+        if (q->shape_eff != p0->shape_eff || q->st.M != p0->st.M || q->var.generic) return false;
+        tiles4 += ((q->pad[2] + 63) / 64) * ((q->pad[0] + 63) / 64);
+    }
+    if (batch2d_variant(p0->shape_eff, p0->st.M, tiles4, &bv)) return false;
+    geo.resize(nshots);
+    for (int i = 0; i < nshots; ++i) {
+        const fd_plan *q = shots[i].plan;
+        const int tx = (int)((q->pad[2] + bv.tx - 1) / bv.tx), tz = (int)((q->pad[0] + bv.tz - 1) / bv.tz);
+        geo[i] = {bv.tx, bv.tz, tx, tx * tz};
+    }
+    return true;
+}
+
+// Instantiated time-loop graphs of batched runs, keyed by workspace, shot
+// pointers and sizes.  At most kGraphCache entries; evicting one synchronises
+// the device first so that no launch of it is pending.
+constexpr size_t kGraphCache = 8;
+std::mutex g_graph_mu;
+std::vector<std::pair<std::vector<uint64_t>, cudaGraphExec_t>> g_graphs;
+
+cudaGraphExec_t graph_cache_find(const std::vector<uint64_t> &key)
+{
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (auto &e : g_graphs)
+        if (e.first == key) return e.second;
+    return nullptr;
+}
+
+void graph_cache_put(const std::vector<uint64_t> &key, cudaGraphExec_t ge)
+{
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    if (g_graphs.size() >= kGraphCache) {
+        cudaDeviceSynchronize();
+        cudaGraphExecDestroy(g_graphs.front().second);
+        g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.emplace_back(key, ge);
+}
+
+size_t batch_extra_bytes(int nshots, int64_t ntiles)
+{
+    return up(nshots * sizeof(ShotDesc)) + 2 * up(ntiles * sizeof(int32_t));
+}
+
+}  // namespace
 
 extern "C" int fd_forward_batched_workspace_size(int nshots, const fd_shot *shots, size_t *bytes)
 {
     clear_error();
     if (nshots < 0 || (nshots > 0 && !shots) || !bytes) return set_error(FD_ERR_ARG, "bad argument");
-    size_t tot = 0;
-    for (int i = 0; i < nshots; ++i) {
+    for (int i = 0; i < nshots; ++i)
         if (!shots[i].plan) return set_error(FD_ERR_ARG, "shot %d has no plan", i);
-        tot += make_layout(shots[i].plan, shots[i].nsrc, shots[i].nrec, false, 1).total;
+    size_t tot = 0;
+    Variant bv;
+    std::vector<TileGeo> geo;
+    const bool one = nshots > 0 && batch_geometry(nshots, shots, bv, geo);
+    int64_t ntiles = 0;
+    for (int i = 0; i < nshots; ++i) {
+        const int nt_tab = one ? geo[i].ntiles : -1;
+        tot += make_layout(shots[i].plan, shots[i].nsrc, shots[i].nrec, false, 1, nt_tab).total;
+        if (one) ntiles += geo[i].ntiles;
     }
+    if (one) tot += batch_extra_bytes(nshots, ntiles);
     *bytes = tot;
     return FD_OK;
 }
@@ -702,93 +938,163 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
     int st = fd_forward_batched_workspace_size(nshots, shots, &need);
     if (st) return st;
     if (!ws || ws_bytes < need) return set_error(FD_ERR_NOMEM, "workspace too small (%zu < %zu)", ws_bytes, need);
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return set_error(FD_ERR_ARG, "workspace must be 256-byte aligned");
     if (nshots == 0) return FD_OK;
     const fd_plan *p0 = shots[0].plan;
     for (int i = 1; i < nshots; ++i) {
         const fd_plan *q = shots[i].plan;
         if (q->prob.dim != p0->prob.dim || q->prob.nt != p0->prob.nt || q->prob.dt != p0->prob.dt ||
-            q->st.M != p0->st.M || q->st.shape != p0->st.shape || q->st.scheme != p0->st.scheme)
+            q->st.M != p0->st.M || q->st.shape != p0->st.shape || q->st.scheme != p0->st.scheme ||
+            std::memcmp(q->W, p0->W, sizeof q->W) != 0)
             return set_error(FD_ERR_ARG, "shot %d: batched shots must share dim, stencil, dt and nt", i);
     }
+    Variant bv;
+    std::vector<TileGeo> geo;
+    const bool one = batch_geometry(nshots, shots, bv, geo);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = reinterpret_cast<char *>(ws);
-    std::vector<StepParams> sps(nshots);
+    std::vector<StepParams> sps(one ? 0 : nshots);
+    std::vector<ShotDesc> descs(one ? nshots : 0);
+    std::vector<int32_t> tshot, tlocal;
     std::vector<float *> As(nshots), Bs(nshots);
     std::vector<const CUtensorMap *> mp(nshots);
     for (int i = 0; i < nshots; ++i) {
         fd_plan *p = const_cast<fd_plan *>(shots[i].plan);
         const fd_shot &sh = shots[i];
-        const Layout L = make_layout(p, sh.nsrc, sh.nrec, false, 1);
+        const Layout L = make_layout(p, sh.nsrc, sh.nrec, false, 1, one ? geo[i].ntiles : -1);
         st = check_common(p, sh.model_kind, sh.model_d, sh.nsrc, sh.src_idx, sh.wavelet_d, sh.nrec,
                           sh.rec_idx, base, L.total, L.total);
         if (st) return set_error(st, "shot %d: %s", i, fd_last_error());
+        if (sh.nrec > 0 && !sh.traces_d) return set_error(FD_ERR_ARG, "shot %d: traces is NULL", i);
         if ((st = ensure_tuned(p))) return st;
         Tables T;
-        if ((st = make_tables(p, sh.nsrc, sh.src_idx, sh.nrec, sh.rec_idx, false, T))) return st;
+        if ((st = make_tables(p, sh.nsrc, sh.src_idx, sh.nrec, sh.rec_idx, false, T,
+                              one ? &geo[i] : nullptr)))
+            return st;
         if ((st = upload_tables(p, L, base, T, s))) return st;
-        if ((st = upload_maps(p, L, base, 2, s))) return st;
         FDW_CK(cudaMemsetAsync(base + L.status, 0, kAlign, s));
         As[i] = reinterpret_cast<float *>(base + L.buf[0]);
         Bs[i] = reinterpret_cast<float *>(base + L.buf[1]);
         FDW_CK(cudaMemsetAsync(As[i], 0, (size_t)p->field * 4, s));
         FDW_CK(cudaMemsetAsync(Bs[i], 0, (size_t)p->field * 4, s));
         if ((st = prep_model(p, L, base, sh.model_kind, sh.model_d, s))) return st;
-        StepParams &sp = sps[i];
-        fill_params(p, sp);
-        sp.kappa = reinterpret_cast<const float *>(base + L.kappa);
-        sp.status = reinterpret_cast<int *>(base + L.status);
-        if (sh.nsrc > 0) {
-            sp.inj_ptr = reinterpret_cast<const int32_t *>(base + L.tab + T.inj_ptr);
-            sp.inj = reinterpret_cast<const PtEntry *>(base + L.tab + T.inj);
-            sp.inj_series = sh.wavelet_d;
-            sp.inj_ncol = sh.nsrc;
+        const int32_t *ip = reinterpret_cast<const int32_t *>(base + L.tab + T.inj_ptr);
+        const PtEntry *ie = reinterpret_cast<const PtEntry *>(base + L.tab + T.inj);
+        const int32_t *sp_ = reinterpret_cast<const int32_t *>(base + L.tab + T.smp_ptr);
+        const PtEntry *se = reinterpret_cast<const PtEntry *>(base + L.tab + T.smp);
+        if (one) {
+            ShotDesc &d = descs[i];
+            std::memset(&d, 0, sizeof d);
+            Variant keep = p->var;
+            p->var = bv;     // maps with the batch's box
+            int r0 = encode_field_map(p, &d.tmap[0], As[i], false);
+            int r1 = encode_field_map(p, &d.tmap[1], Bs[i], false);
+            p->var = keep;
+            if (r0 || r1) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+            d.buf[0] = As[i];
+            d.buf[1] = Bs[i];
+            d.kappa = reinterpret_cast<const float *>(base + L.kappa);
+            d.inj_ptr = sh.nsrc ? ip : nullptr;
+            d.inj = ie;
+            d.inj_series = sh.wavelet_d;
+            d.inj_ncol = sh.nsrc;
+            d.smp_ptr = sh.nrec ? sp_ : nullptr;
+            d.smp = se;
+            d.smp_out = sh.traces_d;
+            d.smp_ncol = sh.nrec;
+            d.nx = p->pad[2];
+            d.nz = p->pad[0];
+            d.pitch = p->pitch;
+            d.phys_lo[0] = p->prob.nb; d.phys_hi[0] = p->prob.nb + p->prob.n[2] - 1;
+            d.phys_lo[2] = p->prob.nb; d.phys_hi[2] = p->prob.nb + p->prob.n[0] - 1;
+            d.gcoef = p->gcoef;
+            d.tiles_x = geo[i].tiles_x;
+            for (int t = 0; t < geo[i].ntiles; ++t) {
+                tshot.push_back(i);
+                tlocal.push_back(t);
+            }
+        } else {
+            if ((st = upload_maps(p, L, base, 2, s))) return st;
+            StepParams &sp = sps[i];
+            fill_params(p, sp);
+            sp.kappa = reinterpret_cast<const float *>(base + L.kappa);
+            sp.status = reinterpret_cast<int *>(base + L.status);
+            if (sh.nsrc > 0) {
+                sp.inj_ptr = ip; sp.inj = ie; sp.inj_series = sh.wavelet_d; sp.inj_ncol = sh.nsrc;
+            }
+            if (sh.nrec > 0) {
+                sp.smp_ptr = sp_; sp.smp = se; sp.smp_out = sh.traces_d; sp.smp_ncol = sh.nrec;
+            }
+            mp[i] = reinterpret_cast<const CUtensorMap *>(base + L.tmaps);
         }
-        if (sh.nrec > 0) {
-            sp.smp_ptr = reinterpret_cast<const int32_t *>(base + L.tab + T.smp_ptr);
-            sp.smp = reinterpret_cast<const PtEntry *>(base + L.tab + T.smp);
-            sp.smp_out = sh.traces_d;
-            sp.smp_ncol = sh.nrec;
-        }
-        mp[i] = reinterpret_cast<const CUtensorMap *>(base + L.tmaps);
         base += L.total;
     }
-    // capture the time loop into a graph (a side stream is used for capture so
-    // that the caller's stream may be the legacy default stream)
-    cudaStream_t cs;
-    FDW_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaEvent_t ev;
-    FDW_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    FDW_CK(cudaEventRecord(ev, s));
-    FDW_CK(cudaStreamWaitEvent(cs, ev, 0));
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    FDW_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaSuccess;
-    const int nt = p0->prob.nt;
-    for (int n = 0; n < nt && ce == cudaSuccess; ++n)
-        for (int i = 0; i < nshots && ce == cudaSuccess; ++i) {
-            StepParams &sp = sps[i];
-            const int cur = n & 1;
-            bind_maps(sp, mp[i], 2, cur, cur ^ 1);
-            sp.u_cur = cur ? Bs[i] : As[i];
-            sp.u_prev = cur ? As[i] : Bs[i];
-            sp.step = n;
-            ce = launch(shots[i].plan, kModeForward, sp, cs);
-        }
-    cudaError_t ee = cudaStreamEndCapture(cs, &g);
-    if (ce != cudaSuccess || ee != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cs);
-        cudaEventDestroy(ev);
-        return set_error(FD_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    BatchParams bp;
+    std::memset(&bp, 0, sizeof bp);
+    const int ntiles = (int)tshot.size();
+    if (one) {
+        char *d = base;
+        FDW_CK(cudaMemcpyAsync(d, descs.data(), nshots * sizeof(ShotDesc), cudaMemcpyHostToDevice, s));
+        char *t1 = d + up(nshots * sizeof(ShotDesc));
+        char *t2 = t1 + up(ntiles * sizeof(int32_t));
+        FDW_CK(cudaMemcpyAsync(t1, tshot.data(), ntiles * 4, cudaMemcpyHostToDevice, s));
+        FDW_CK(cudaMemcpyAsync(t2, tlocal.data(), ntiles * 4, cudaMemcpyHostToDevice, s));
+        bp.shots = reinterpret_cast<const ShotDesc *>(d);
+        bp.tile_shot = reinterpret_cast<const int32_t *>(t1);
+        bp.tile_local = reinterpret_cast<const int32_t *>(t2);
+        // shot 0's status word collects the device conditions of the batch
+        bp.status = reinterpret_cast<int *>(ws);
+        std::memcpy(bp.w, p0->W, sizeof bp.w);
     }
-    FDW_CK(cudaGraphInstantiate(&ge, g, 0));
-    FDW_CK(cudaGraphLaunch(ge, cs));
-    FDW_CK(cudaEventRecord(ev, cs));
-    FDW_CK(cudaStreamWaitEvent(s, ev, 0));
-    cudaGraphExecDestroy(ge);
-    cudaGraphDestroy(g);
-    cudaStreamDestroy(cs);
-    cudaEventDestroy(ev);
+    // The time loop is captured once per (workspace, shots) configuration and
+    // replayed on later calls; all per-call state (models, tables, fields) is
+    // re-initialised above, outside the graph.
+    std::vector<uint64_t> key;
+    key.push_back(reinterpret_cast<uint64_t>(ws));
+    key.push_back((uint64_t)nshots);
+    for (int i = 0; i < nshots; ++i) {
+        const fd_shot &sh = shots[i];
+        key.push_back(reinterpret_cast<uint64_t>(sh.plan));
+        key.push_back(reinterpret_cast<uint64_t>(sh.wavelet_d));
+        key.push_back(reinterpret_cast<uint64_t>(sh.traces_d));
+        key.push_back(((uint64_t)(uint32_t)sh.nsrc << 32) | (uint32_t)sh.nrec);
+    }
+    cudaGraphExec_t ge = graph_cache_find(key);
+    if (!ge) {
+        cudaStream_t cs;
+        FDW_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        FDW_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaSuccess;
+        const int nt = p0->prob.nt;
+        for (int n = 0; n < nt && ce == cudaSuccess; ++n) {
+            if (one) {
+                bp.step = n;
+                ce = launch_batched2d(bv, bp, ntiles, cs);
+                continue;
+            }
+            for (int i = 0; i < nshots && ce == cudaSuccess; ++i) {
+                StepParams &sp = sps[i];
+                const int cur = n & 1;
+                bind_maps(sp, mp[i], 2, cur, cur ^ 1);
+                sp.u_cur = cur ? Bs[i] : As[i];
+                sp.u_prev = cur ? As[i] : Bs[i];
+                sp.step = n;
+                ce = launch(shots[i].plan, kModeForward, sp, cs);
+            }
+        }
+        cudaError_t ee = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return set_error(FD_ERR_CUDA, "graph capture failed: %s",
+                             cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+        }
+        cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return set_error(FD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+        graph_cache_put(key, ge);
+    }
+    FDW_CK(cudaGraphLaunch(ge, s));
     return FD_OK;
 }

@@ -32,17 +32,16 @@ __device__ __forceinline__ void for_owned(const int32_t *ptr, const PtEntry *tab
     }
 }
 
-template <int SHAPE, int M, int NN, int MODE, int R>
-__global__ void __launch_bounds__(kThreads) step2d_kernel(const __grid_constant__ StepParams p)
+// One tile of the 2D step.  PP is the parameter view: StepParams for a
+// single-shot launch, BatchView (below) for a launch over many shots.
+template <int SHAPE, int M, int NN, int MODE, int R, class PP>
+__device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *sm, uint64_t &bar)
 {
     constexpr int HX = round4(M);
     constexpr int SW = kTX + 2 * HX;
     constexpr int SH = kTZ * R + 2 * M;
-    extern __shared__ __align__(1024) float sm[];
-    __shared__ uint64_t bar;
 
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int tile = blockIdx.x;
     const int x0 = (tile % p.tiles_x) * kTX;
     const int z0 = (tile / p.tiles_x) * (kTZ * R);
 
@@ -165,6 +164,66 @@ __global__ void __launch_bounds__(kThreads) step2d_kernel(const __grid_constant_
     }
 }
 
+template <int SHAPE, int M, int NN, int MODE, int R>
+__global__ void __launch_bounds__(kThreads) step2d_kernel(const __grid_constant__ StepParams p)
+{
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t bar;
+    step2d_tile<SHAPE, M, NN, MODE, R>(p, blockIdx.x, sm, bar);
+}
+
+// ---------------------------------------------------------------------------
+// Batched shots: one launch per time step over the tiles of every shot.  A
+// CTA finds its shot and local tile in two tables and reads the shot's
+// descriptor (tensor maps of both field buffers, pointers, sizes, point
+// tables) from device memory; the weights stay in kernel parameters.
+// ---------------------------------------------------------------------------
+struct BatchView {
+    const CUtensorMap *tmap;
+    float *u_prev;
+    const float *kappa;
+    int64_t nx, nz, pitch;
+    int64_t phys_lo[3], phys_hi[3];
+    float gcoef;
+    int tiles_x;
+    const int32_t *inj_ptr;
+    const PtEntry *inj;
+    const float *inj_series;
+    int inj_ncol;
+    const int32_t *smp_ptr;
+    const PtEntry *smp;
+    float *smp_out;
+    int smp_ncol;
+    int step;
+    float *dseg_out;
+    const float *dseg_in;
+    float *gacc;
+    int *status;
+    const float (&w)[kWDim * kWDim];
+    __device__ BatchView(const ShotDesc &d, const BatchParams &bp)
+        : tmap(&d.tmap[bp.step & 1]), u_prev(d.buf[(bp.step & 1) ^ 1]), kappa(d.kappa), nx(d.nx),
+          nz(d.nz), pitch(d.pitch), gcoef(d.gcoef), tiles_x(d.tiles_x), inj_ptr(d.inj_ptr),
+          inj(d.inj), inj_series(d.inj_series), inj_ncol(d.inj_ncol), smp_ptr(d.smp_ptr),
+          smp(d.smp), smp_out(d.smp_out), smp_ncol(d.smp_ncol), step(bp.step), dseg_out(nullptr),
+          dseg_in(nullptr), gacc(nullptr), status(bp.status), w(bp.w)
+    {
+        for (int i = 0; i < 3; ++i) {
+            phys_lo[i] = d.phys_lo[i];
+            phys_hi[i] = d.phys_hi[i];
+        }
+    }
+};
+
+template <int SHAPE, int M, int R>
+__global__ void __launch_bounds__(kThreads) step2d_batched(const __grid_constant__ BatchParams bp)
+{
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t bar;
+    const int g = blockIdx.x;
+    const BatchView v(bp.shots[bp.tile_shot[g]], bp);
+    step2d_tile<SHAPE, M, 0, kModeForward, R>(v, bp.tile_local[g], sm, bar);
+}
+
 // Generic runtime-shape 2D kernel (any shape, 1 <= M <= kMaxM): scalar
 // shared-memory reads, one row per thread (R = 1).
 template <int MODE>
@@ -282,9 +341,59 @@ KernelFn lookup_fast(int shape, int M, int R, int mode)
     return nullptr;
 }
 
+using BatchFn = void (*)(const BatchParams);
+
+BatchFn lookup_batched(int shape, int M, int R)
+{
+#define FDW_B(S, MM, RR) \
+    if (shape == S && M == MM && R == RR) return step2d_batched<S, MM, RR>;
+    FDW_B(FD_CROSS, 2, 1) FDW_B(FD_CROSS, 4, 1) FDW_B(FD_CROSS, 8, 1)
+    FDW_B(FD_CROSS, 2, 4) FDW_B(FD_CROSS, 4, 4) FDW_B(FD_CROSS, 8, 4)
+#undef FDW_B
+    return nullptr;
+}
+
 }  // namespace
 
-int select_variant_2d(int shape, int M, int N, int64_t nx, int64_t nz, Variant *v)
+int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v)
+{
+    const int R = total_tiles4 >= 2 * 152 ? 4 : 1;
+    if (!lookup_batched(shape, M, R)) return FD_ERR_UNSUPPORTED;
+    v->dim = 2;
+    v->shape = shape;
+    v->M = M;
+    v->N = 0;
+    v->generic = 0;
+    v->threads = kThreads;
+    v->tx = kTX;
+    v->tz = kTZ * R;
+    v->box[0] = kTX + 2 * round4(M);
+    v->box[1] = kTZ * R + 2 * M;
+    v->box[2] = 1;
+    v->smem = (size_t)v->box[0] * v->box[1] * sizeof(float);
+    return FD_OK;
+}
+
+cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s)
+{
+    BatchFn fn = lookup_batched(v.shape, v.M, v.tz / kTZ);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    if (e != cudaSuccess) return e;
+    if (ntiles <= 0) return cudaSuccess;
+    fn<<<ntiles, kThreads, v.smem, s>>>(bp);
+    return cudaGetLastError();
+}
+
+int variants_2d(int shape, int M, int *r_out, int cap)
+{
+    int n = 0;
+    for (int r : {4, 1})
+        if (n < cap && lookup_fast(shape, M, r, 0)) r_out[n++] = r;
+    return n;
+}
+
+int select_variant_2d(int shape, int M, int N, int64_t nx, int64_t nz, Variant *v, int r_pref)
 {
     v->dim = 2;
     v->shape = shape;
@@ -295,7 +404,7 @@ int select_variant_2d(int shape, int M, int N, int64_t nx, int64_t nz, Variant *
     // R = 4 rows per thread when the grid has enough tiles to fill the GPU
     // (two CTAs per SM on 152 SMs), else one row per thread.
     const int64_t tiles4 = ((nx + kTX - 1) / kTX) * ((nz + 4 * kTZ - 1) / (4 * kTZ));
-    int R = tiles4 >= 2 * 152 ? 4 : 1;
+    int R = r_pref > 0 ? r_pref : (tiles4 >= 2 * 152 ? 4 : 1);
     if (!lookup_fast(shape, M, R, 0)) R = 5 - R;
     v->generic = lookup_fast(shape, M, R, 0) ? 0 : 1;
     if (v->generic) R = 1;

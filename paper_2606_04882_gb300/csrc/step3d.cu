@@ -399,15 +399,28 @@ step3d_cross(const __grid_constant__ StepParams p)
     uint32_t fph = 0;
     bool ok = true;
 
-    // stream index s = -2M + QL*k + u; the queue slot of the plane fed at s is u
-    for (int k0 = 0; k0 < S; k0 += QL) {
+    // Queue addressing: unrolled (M <= 4), the plane fed at stream index s sits
+    // in slot s mod QL and the loop is unrolled by QL; shifted (M >= 6, to keep
+    // the code small), slot QL-1 always holds the newest plane and the queue
+    // moves down one slot per plane.
+    constexpr bool kUnroll = M <= 4;
+    constexpr int UF = kUnroll ? QL : 1;
+    for (int k0 = 0; k0 < S; k0 += UF) {
 #pragma unroll
-        for (int u = 0; u < QL; ++u) {
-            const int si = k0 + u;            // 0-based stream index
+        for (int uu = 0; uu < UF; ++uu) {
+            const int si = k0 + uu;            // 0-based stream index
             if (si >= S) break;
+            const int u = kUnroll ? uu : QL - 1;   // slot of the plane fed now
             ok = ok && mbar_wait_bounded(&full[slot], fph);
             if (!ok) break;
             const float *P = sm + slot * SLOT;
+            if (!kUnroll) {
+#pragma unroll
+                for (int i = 0; i < QL - 1; ++i) {
+                    qa[i] = qa[i + 1];
+                    qb[i] = qb[i + 1];
+                }
+            }
             ld4x2(P + C::AEL + 2 * C::TEL + cT, qa[u], qb[u]);   // plane zb + si - M
             if (si >= 2 * M) {
                 const int z = zb + si - 2 * M;
@@ -772,11 +785,13 @@ KernelFn lookup3(int shape, int M, int ty, int mode)
 #define FDW_Q(MM, TT) \
     if (shape == FD_CROSS && M == MM && ty == TT) return pick_cross<MM, TT>(mode);
     FDW_Q(1, 16) FDW_Q(2, 16) FDW_Q(3, 16) FDW_Q(4, 16) FDW_Q(6, 8) FDW_Q(8, 8)
+    FDW_Q(2, 8) FDW_Q(4, 8)
 #undef FDW_Q
 #define FDW_P(S, MM, TT) \
     if (shape == S && M == MM && ty == TT) return pick_planar<S, MM, TT>(mode);
     FDW_P(FD_RHOMBUS, 2, 16) FDW_P(FD_RHOMBUS, 3, 16) FDW_P(FD_RHOMBUS, 4, 16)
     FDW_P(FD_RHOMBUS, 6, 8) FDW_P(FD_RHOMBUS, 8, 8) FDW_P(FD_SQUARE, 2, 16) FDW_P(FD_SQUARE, 4, 16)
+    FDW_P(FD_RHOMBUS, 4, 8)
 #undef FDW_P
     return nullptr;
 #define FDW_C(S, MM, TT) \
@@ -790,14 +805,15 @@ KernelFn lookup3(int shape, int M, int ty, int mode)
 
 }  // namespace
 
-int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t nz, Variant *v)
+int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t nz, Variant *v,
+                      int ty_pref)
 {
     v->dim = 3;
     v->shape = shape;
     v->M = M;
     v->N = N;
     v->generic = 0;
-    int ty = M <= 4 ? 16 : 8;
+    int ty = ty_pref > 0 ? ty_pref : (M <= 4 ? 16 : 8);
     if (!lookup3(shape, M, ty, 0)) return FD_ERR_UNSUPPORTED;
     v->tx = kTX3;
     v->tz = ty;
@@ -817,6 +833,14 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
     }
     (void)nx; (void)ny; (void)nz;
     return 0;
+}
+
+int variants_3d(int shape, int M, int *ty_out, int cap)
+{
+    int n = 0;
+    for (int ty : {16, 8})
+        if (n < cap && lookup3(shape, M, ty, 0)) ty_out[n++] = ty;
+    return n;
 }
 
 cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s)

@@ -129,3 +129,30 @@ def test_velocity_above_vmax_is_reported():
     c = Case(vel, 10.0, 5, 2, 2500.0, "cross", 2, src=[[10, 10]], rec=[[1, 1]])
     _, _, rc = c.gpu_forward()
     assert rc == F.FD_ERR_UNSTABLE
+
+
+@pytest.mark.parametrize("dim,shape,M,scheme", [(3, "cross", 4, "spatte"), (3, "rhombus", 4, "displs"),
+                                                (2, "cross", 4, "spatte")])
+def test_autotune_keeps_results_bitwise(dim, shape, M, scheme):
+    """The tile shape the autotuner picks changes the schedule, not the
+    arithmetic of any point: traces and fields are bitwise identical."""
+    import torch
+    import paper_2606_04882_gb300 as F
+    n = (120, 150) if dim == 2 else (40, 44, 70)
+    vel = smooth_velocity(n, 12, 1500.0, 3000.0, sigma=3.0)
+    rec = np.array([[2] * (dim - 1) + [x] for x in range(0, n[-1], 3)])
+    c = Case(vel, 10.0, 40, 8, 3000.0, shape, M, 0, scheme, src=[[s // 2 for s in n]], rec=rec)
+    tr0, st0, _ = c.gpu_forward()
+    plan = c.plan()
+    plan.autotune(torch.from_numpy(c.vel).cuda())
+    after = plan.info()
+    dev = torch.device("cuda")
+    tr = torch.zeros((c.nt, len(rec)), device=dev)
+    ws = F.workspace(plan.forward_workspace_size(1, len(rec)))
+    F.fd_forward(plan, torch.from_numpy(c.vel).to(dev), plan.linear_index(c.src),
+                 torch.from_numpy(c.wavelet32()).to(dev), plan.linear_index(c.rec), tr, ws)
+    assert np.array_equal(tr.cpu().numpy(), tr0)
+    # a second plan of the same problem takes the cached choice
+    p2 = c.plan()
+    p2.autotune(torch.from_numpy(c.vel).cuda())
+    assert tuple(p2.info().tile) == tuple(after.tile)
