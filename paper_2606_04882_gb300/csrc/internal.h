@@ -25,9 +25,12 @@ struct PtEntry {
     float scale;     // value factor
 };
 
+// Launch modes.  Forward and store-D run the same kernel instantiation (the
+// D store is a runtime branch on dseg_out), so the checkpointed recompute of
+// the gradient reproduces the forward sweep bitwise.
 enum Mode : int {
     kModeForward = 0,     // plain step: inject sources, sample receivers
-    kModeStoreD = 1,      // forward step that also writes D = kappa * lap to dseg
+    kModeStoreD = 1,      // forward step that also writes D = kappa * lap to dseg_out
     kModeAdjoint = 2      // adjoint step (q-form) with gradient accumulation
 };
 
@@ -65,6 +68,9 @@ struct StepParams {
     float *gacc;               // kModeAdjoint: accumulator (same layout as fields)
     int *status;
     float w[kWDim * kWDim];    // symmetric weight table W[p][q] = a_orbit(max, min)
+    // 3D planar kernels: zarm[i] = sum_{s >= i} A_s, A_s the total weight of
+    // the points at |dz| = s (zarm[M + 1] = 0)
+    float zarm[kWDim];
 };
 
 // Batched 2D shots: per-shot descriptor in device memory (64-byte aligned for
@@ -94,6 +100,18 @@ struct BatchParams {
     float w[kWDim * kWDim];
 };
 
+// Persistent 2D time loop: step parameters plus both buffers' maps and the
+// grid-barrier words (in the workspace's status block).
+struct PersistParams {
+    StepParams base;
+    const CUtensorMap *maps;   // halo-box map of buffer b at maps[2 b] (workspace map layout)
+    float *buf[2];
+    int nt;
+    unsigned int *bar_count;
+    unsigned int *bar_gen;
+    int *abort_flag;
+};
+
 // Kernel variant descriptor chosen by the plan.
 struct Variant {
     int dim, shape, M, N;
@@ -115,6 +133,8 @@ int variants_3d(int shape, int M, int *ty_out, int cap);
 cudaError_t launch_step2d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
 cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
 int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v);
+int persist2d_grid(const Variant &v, int ntiles);
+cudaError_t launch_persist2d(const Variant &v, const PersistParams &pp, int grid, cudaStream_t s);
 cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s);
 
 // aux kernels

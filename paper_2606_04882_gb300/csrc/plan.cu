@@ -1,6 +1,7 @@
 // Host runtime of libfdwave: plans, workspace layout, point tables, the
 // forward time loop, the checkpointed adjoint gradient and batched shots.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -10,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "device_common.cuh"
 #include "internal.h"
 #include "runtime.h"
 
@@ -30,6 +32,7 @@ struct fd_plan {
     float gcoef = 0.f;
     float W[fdw::kWDim * fdw::kWDim];
     void *last_ws = nullptr;
+    uint64_t id = 0;   // unique per created plan (never reused: keys the graph cache)
 };
 
 namespace fdw {
@@ -263,6 +266,20 @@ void fill_params(const fd_plan *p, StepParams &sp)
     sp.zchunk = p->zchunk;
     sp.nz_chunks = p->nz_chunks;
     std::memcpy(sp.w, p->W, sizeof sp.w);
+    // z-axis weight sums of the planar 3D kernels, from the FP32 table
+    const int M = p->st.M;
+    double A[kWDim + 1] = {0.0};
+    for (int s = 1; s <= M && s < kWDim; ++s) {
+        const int E = shape_ext(p->shape_eff, M, 0, s);
+        double a = p->W[s];
+        for (int pp = 1; pp <= E; ++pp) a += 4.0 * p->W[pp * kWDim + s];
+        A[s] = a;
+    }
+    double B = 0.0;
+    for (int i = std::min(M, kWDim - 1); i >= 1; --i) {
+        B += A[i];
+        sp.zarm[i] = (float)B;
+    }
 }
 
 cudaError_t launch(const fd_plan *p, int mode, const StepParams &sp, cudaStream_t s)
@@ -350,6 +367,8 @@ extern "C" int fd_plan_create(const fd_problem *prob, const fd_stencil_desc *ste
         return set_error(FD_ERR_ARG, "grid too large for the tile tables");
     fd_plan *p = new (std::nothrow) fd_plan();
     if (!p) return set_error(FD_ERR_NOMEM, "host allocation failed");
+    static std::atomic<uint64_t> next_id{1};
+    p->id = next_id.fetch_add(1);
     p->prob = pr;
     p->st = *stencil;
     int st = compute_weights(stencil, p->keys, p->mult, p->w, nullptr, nullptr);
@@ -620,6 +639,34 @@ int upload_maps(fd_plan *p, const Layout &L, char *ws, int nbuf, cudaStream_t s)
     return FD_OK;
 }
 
+// Instantiated time-loop graphs (single-shot and batched runs), keyed by
+// workspace address, plan ids (never reused, unlike addresses), data
+// pointers, sizes and kernel variant.  Every per-call state lives in the
+// workspace and is re-initialised before a replay.  At most kGraphCache entries; evicting one synchronises
+// the device first so that no launch of it is pending.
+constexpr size_t kGraphCache = 8;
+std::mutex g_graph_mu;
+std::vector<std::pair<std::vector<uint64_t>, cudaGraphExec_t>> g_graphs;
+
+cudaGraphExec_t graph_cache_find(const std::vector<uint64_t> &key)
+{
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    for (auto &e : g_graphs)
+        if (e.first == key) return e.second;
+    return nullptr;
+}
+
+void graph_cache_put(const std::vector<uint64_t> &key, cudaGraphExec_t ge)
+{
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    if (g_graphs.size() >= kGraphCache) {
+        cudaDeviceSynchronize();
+        cudaGraphExecDestroy(g_graphs.front().second);
+        g_graphs.erase(g_graphs.begin());
+    }
+    g_graphs.emplace_back(key, ge);
+}
+
 // stride between consecutive z (rows in 2D, planes in 3D), in floats
 int64_t zstride(const fd_plan *p) { return p->prob.dim == 3 ? p->plane : p->pitch; }
 
@@ -705,13 +752,72 @@ extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int ns
         sp.smp_out = traces;
         sp.smp_ncol = nrec;
     }
-    for (int n = 0; n < p->prob.nt; ++n) {
-        const int cur = n & 1;
-        bind_maps(sp, maps, 2, cur, cur ^ 1);
-        sp.u_cur = cur ? B : A;
-        sp.u_prev = cur ? A : B;
-        sp.step = n;
-        FDW_CK(launch(p, kModeForward, sp, s));
+    // Time loop: one cooperative persistent launch when asked for (small 2D
+    // grids, FDWAVE_PERSISTENT=1), else one launch per step, captured once
+    // into a CUDA graph per (workspace, plan, pointers, variant) and replayed
+    // (FDWAVE_GRAPHS=0: plain launches).
+    int pgrid = 0;
+    {
+        const char *e = getenv("FDWAVE_PERSISTENT");
+        if (e && e[0] == '1' && p->prob.dim == 2 && p->prob.nt >= 16 && !p->var.generic)
+            pgrid = persist2d_grid(p->var, p->ntiles);
+    }
+    auto step_loop = [&](cudaStream_t ls) -> cudaError_t {
+        for (int n = 0; n < p->prob.nt; ++n) {
+            const int cur = n & 1;
+            bind_maps(sp, maps, 2, cur, cur ^ 1);
+            sp.u_cur = cur ? B : A;
+            sp.u_prev = cur ? A : B;
+            sp.step = n;
+            cudaError_t e = launch(p, kModeForward, sp, ls);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    const char *ge_env = getenv("FDWAVE_GRAPHS");
+    const bool use_graph = pgrid == 0 && p->prob.nt >= 16 && !(ge_env && ge_env[0] == '0');
+    if (pgrid > 0) {
+        PersistParams pp;
+        std::memset(&pp, 0, sizeof pp);
+        pp.base = sp;
+        pp.maps = maps;
+        pp.buf[0] = A;
+        pp.buf[1] = B;
+        pp.nt = p->prob.nt;
+        int *stw = reinterpret_cast<int *>(w + L.status);
+        pp.abort_flag = stw + 1;
+        pp.bar_count = reinterpret_cast<unsigned int *>(stw + 2);
+        pp.bar_gen = reinterpret_cast<unsigned int *>(stw + 3);
+        FDW_CK(launch_persist2d(p->var, pp, pgrid, s));
+    } else if (use_graph) {
+        const std::vector<uint64_t> key = {
+            1ull, reinterpret_cast<uint64_t>(ws), p->id,
+            reinterpret_cast<uint64_t>(wavelet), reinterpret_cast<uint64_t>(traces),
+            ((uint64_t)(uint32_t)nsrc << 32) | (uint32_t)nrec, (uint64_t)p->prob.nt,
+            ((uint64_t)p->var.tz << 32) | (uint32_t)p->zchunk,
+            ((uint64_t)p->var.threads << 32) | (uint32_t)p->var.generic};
+        cudaGraphExec_t ge = graph_cache_find(key);
+        if (!ge) {
+            cudaStream_t cs;
+            FDW_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            FDW_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            const cudaError_t ce = step_loop(cs);
+            const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+            cudaStreamDestroy(cs);
+            if (ce != cudaSuccess || ee != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return set_error(FD_ERR_CUDA, "graph capture failed: %s",
+                                 cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+            }
+            const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) return set_error(FD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+            graph_cache_put(key, ge);
+        }
+        FDW_CK(cudaGraphLaunch(ge, s));
+    } else {
+        FDW_CK(step_loop(s));
     }
     if (state_out_d) {
         const bool even = (p->prob.nt % 2) == 0;
@@ -876,32 +982,6 @@ bool batch_geometry(int nshots, const fd_shot *shots, Variant &bv, std::vector<T
     return true;
 }
 
-// Instantiated time-loop graphs of batched runs, keyed by workspace, shot
-// pointers and sizes.  At most kGraphCache entries; evicting one synchronises
-// the device first so that no launch of it is pending.
-constexpr size_t kGraphCache = 8;
-std::mutex g_graph_mu;
-std::vector<std::pair<std::vector<uint64_t>, cudaGraphExec_t>> g_graphs;
-
-cudaGraphExec_t graph_cache_find(const std::vector<uint64_t> &key)
-{
-    std::lock_guard<std::mutex> lock(g_graph_mu);
-    for (auto &e : g_graphs)
-        if (e.first == key) return e.second;
-    return nullptr;
-}
-
-void graph_cache_put(const std::vector<uint64_t> &key, cudaGraphExec_t ge)
-{
-    std::lock_guard<std::mutex> lock(g_graph_mu);
-    if (g_graphs.size() >= kGraphCache) {
-        cudaDeviceSynchronize();
-        cudaGraphExecDestroy(g_graphs.front().second);
-        g_graphs.erase(g_graphs.begin());
-    }
-    g_graphs.emplace_back(key, ge);
-}
-
 size_t batch_extra_bytes(int nshots, int64_t ntiles)
 {
     return up(nshots * sizeof(ShotDesc)) + 2 * up(ntiles * sizeof(int32_t));
@@ -1054,11 +1134,12 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
     key.push_back((uint64_t)nshots);
     for (int i = 0; i < nshots; ++i) {
         const fd_shot &sh = shots[i];
-        key.push_back(reinterpret_cast<uint64_t>(sh.plan));
+        key.push_back(sh.plan->id);
         key.push_back(reinterpret_cast<uint64_t>(sh.wavelet_d));
         key.push_back(reinterpret_cast<uint64_t>(sh.traces_d));
         key.push_back(((uint64_t)(uint32_t)sh.nsrc << 32) | (uint32_t)sh.nrec);
     }
+    key.insert(key.begin(), 2ull);
     cudaGraphExec_t ge = graph_cache_find(key);
     if (!ge) {
         cudaStream_t cs;

@@ -88,36 +88,70 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
     for (int r = 0; r < R; ++r) {
         const int zl = M + ty * R + r;
         const int zg = z0 + ty * R + r;
+        const float4 c = ld4(sm + zl * SW + HX + 4 * tx);
+        const float cc[4] = {c.x, c.y, c.z, c.w};
+        float u2[4], u4[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            u2[j] = cc[j] + cc[j];
+            u4[j] = u2[j] + u2[j];
+        }
+        // Centre-free Laplacian: sum_o a_o (u(x+o) - u(x)), the same sum since
+        // the weights of a consistent stencil add up to zero.  Each group of n
+        // points has n u(x) subtracted before it is weighted, so a constant
+        // field gives exactly zero whatever the FP32 rounding of the weights,
+        // and the accumulator only holds small differences.
         float lap[4] = {0.f, 0.f, 0.f, 0.f};
+        if (SHAPE == FD_CROSS) {
+            // x and z arms of offset m share the weight W[0][m]
+            float win[4 + 2 * HX];
 #pragma unroll
-        for (int q = 0; q <= M; ++q) {
-            const int E = shape_ext(SHAPE, M, NN, q);
-            if (E < 0) continue;
-            const int E4 = round4(E);
-            float win[4 + 2 * round4(M)];
-            const float *rp = sm + (zl + q) * SW + HX + 4 * tx - E4;
-            const float *rm = sm + (zl - q) * SW + HX + 4 * tx - E4;
-#pragma unroll
-            for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
-                float4 a = ld4(rp + 4 * i);
-                if (q > 0) {
-                    const float4 b = ld4(rm + 4 * i);
-                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-                }
+            for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
+                const float4 a = ld4(sm + zl * SW + 4 * tx + 4 * i);
                 win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float acc = p.w[q] * win[E4 + j];   // W[0][q]
+            for (int m = 1; m <= M; ++m) {
+                const float4 a = ld4(sm + (zl + m) * SW + HX + 4 * tx);
+                const float4 b = ld4(sm + (zl - m) * SW + HX + 4 * tx);
+                const float zp[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
 #pragma unroll
-                for (int pp = 1; pp <= E; ++pp)
-                    acc = fmaf(p.w[pp * kWDim + q], win[E4 + j + pp] + win[E4 + j - pp], acc);
-                lap[j] += acc;
+                for (int j = 0; j < 4; ++j)
+                    lap[j] = fmaf(p.w[m], ((win[HX + j + m] + win[HX + j - m]) + zp[j]) - u4[j],
+                                  lap[j]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q <= M; ++q) {
+                const int E = shape_ext(SHAPE, M, NN, q);
+                if (E < 0) continue;
+                const int E4 = round4(E);
+                float win[4 + 2 * round4(M)];
+                const float *rp = sm + (zl + q) * SW + HX + 4 * tx - E4;
+                const float *rm = sm + (zl - q) * SW + HX + 4 * tx - E4;
+#pragma unroll
+                for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
+                    float4 a = ld4(rp + 4 * i);
+                    if (q > 0) {
+                        const float4 b = ld4(rm + 4 * i);
+                        a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                    }
+                    win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    // row pair z +- q holds 2 points at dx = 0 and 4 at dx = +-pp;
+                    // row z holds the centre (no term) and 2 points at +-pp
+                    const float un = q > 0 ? u4[j] : u2[j];
+                    float acc = q > 0 ? p.w[q] * (win[E4 + j] - u2[j]) : 0.f;   // W[0][q]
+#pragma unroll
+                    for (int pp = 1; pp <= E; ++pp)
+                        acc = fmaf(p.w[pp * kWDim + q], (win[E4 + j + pp] + win[E4 + j - pp]) - un, acc);
+                    lap[j] += acc;
+                }
             }
         }
-        const float4 c = ld4(sm + zl * SW + HX + 4 * tx);
         const float d2z = layer_d2(zg, p.phys_lo[2], p.phys_hi[2]);
-        const float cc[4] = {c.x, c.y, c.z, c.w};
         const float uu[4] = {up[r].x, up[r].y, up[r].z, up[r].w};
         const float kk[4] = {kp[r].x, kp[r].y, kp[r].z, kp[r].w};
         float o[4], dv[4], g[4];
@@ -152,7 +186,7 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
         const int64_t off = (int64_t)zg * p.pitch + xg;
         const float4 un = make_float4(o[0], o[1], o[2], o[3]);
         *reinterpret_cast<float4 *>(p.u_prev + off) = un;
-        if (MODE == kModeStoreD)
+        if (MODE != kModeAdjoint && p.dseg_out)
             *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
         if (MODE == kModeAdjoint) {
             const float4 d = ldg4(p.dseg_in + off);
@@ -224,6 +258,107 @@ __global__ void __launch_bounds__(kThreads) step2d_batched(const __grid_constant
     step2d_tile<SHAPE, M, 0, kModeForward, R>(v, bp.tile_local[g], sm, bar);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent time loop for small grids (fields resident in L2), where the
+// latency of one launch per step dominates: a cooperative launch keeps every
+// CTA resident; CTAs loop over the time steps and take their tiles of each
+// step in turn, separated by a grid barrier.  The barrier spins with a time
+// bound and an abort flag: on a time-out the status bit is set, the flag
+// raised, and every CTA leaves at its next barrier.  After the barrier the
+// TMA-issuing thread executes a generic->async proxy fence, so the field
+// written in the previous step by other CTAs is what the next TMA loads read.
+// ---------------------------------------------------------------------------
+struct StepView {
+    const CUtensorMap *tmap;
+    float *u_prev;
+    const float *kappa;
+    int64_t nx, nz, pitch;
+    int64_t phys_lo[3], phys_hi[3];
+    float gcoef;
+    int tiles_x;
+    const int32_t *inj_ptr;
+    const PtEntry *inj;
+    const float *inj_series;
+    int inj_ncol;
+    const int32_t *smp_ptr;
+    const PtEntry *smp;
+    float *smp_out;
+    int smp_ncol;
+    int step;
+    float *dseg_out;
+    const float *dseg_in;
+    float *gacc;
+    int *status;
+    const float (&w)[kWDim * kWDim];
+    __device__ StepView(const PersistParams &pp, int n)
+        : tmap(pp.maps + 2 * (n & 1)), u_prev(pp.buf[(n & 1) ^ 1]), kappa(pp.base.kappa),
+          nx(pp.base.nx), nz(pp.base.nz), pitch(pp.base.pitch), gcoef(pp.base.gcoef),
+          tiles_x(pp.base.tiles_x), inj_ptr(pp.base.inj_ptr), inj(pp.base.inj),
+          inj_series(pp.base.inj_series), inj_ncol(pp.base.inj_ncol), smp_ptr(pp.base.smp_ptr),
+          smp(pp.base.smp), smp_out(pp.base.smp_out), smp_ncol(pp.base.smp_ncol), step(n),
+          dseg_out(nullptr), dseg_in(nullptr), gacc(nullptr), status(pp.base.status), w(pp.base.w)
+    {
+        for (int i = 0; i < 3; ++i) {
+            phys_lo[i] = pp.base.phys_lo[i];
+            phys_hi[i] = pp.base.phys_hi[i];
+        }
+    }
+};
+
+// Grid-wide barrier; false if it timed out here or another CTA aborted.
+__device__ __forceinline__ bool grid_sync(const PersistParams &pp)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int *gen = pp.bar_gen;
+        volatile int *abort_v = pp.abort_flag;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int a = atomicAdd(pp.bar_count, 1u) + 1u;
+        if (a == gridDim.x) {
+            atomicExch(pp.bar_count, 0u);
+            __threadfence();
+            atomicAdd(pp.bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (*abort_v) {
+                    ok = 0;
+                    break;
+                }
+                if (clock64() - t0 > 4000000000LL) {
+                    atomicOr(pp.base.status, kStatusTimeout);
+                    *abort_v = 1;
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <int SHAPE, int M, int R>
+__global__ void __launch_bounds__(kThreads) step2d_persistent(const __grid_constant__ PersistParams pp)
+{
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t bar;
+    const int ntiles = pp.base.tiles_x * pp.base.tiles_y;
+    for (int n = 0; n < pp.nt; ++n) {
+        const StepView v(pp, n);
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+            step2d_tile<SHAPE, M, 0, kModeForward, R>(v, t, sm, bar);
+        if (n + 1 < pp.nt && !grid_sync(pp)) return;
+    }
+}
+
 // Generic runtime-shape 2D kernel (any shape, 1 <= M <= kMaxM): scalar
 // shared-memory reads, one row per thread (R = 1).
 template <int MODE>
@@ -268,21 +403,23 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
     const float d2z = layer_d2(zg, p.phys_lo[2], p.phys_hi[2]);
     for (int j = 0; j < 4; ++j) {
         const int xc = HX + 4 * tx + j;
+        // centre-free Laplacian (see step2d_tile)
+        const float c = sm[zl * SW + xc];
+        const float u2 = c + c, u4 = u2 + u2;
         float lap = 0.f;
         for (int q = 0; q <= M; ++q) {
             const int E = shape_ext(shape, M, N, q);
             if (E < 0) continue;
             const float *rp = sm + (zl + q) * SW + xc;
             const float *rm = sm + (zl - q) * SW + xc;
-            float acc = p.w[q] * (q ? rp[0] + rm[0] : rp[0]);
+            float acc = q ? p.w[q] * ((rp[0] + rm[0]) - u2) : 0.f;
             for (int pp = 1; pp <= E; ++pp) {
                 float s = rp[pp] + rp[-pp];
                 if (q) s += rm[pp] + rm[-pp];
-                acc = fmaf(p.w[pp * kWDim + q], s, acc);
+                acc = fmaf(p.w[pp * kWDim + q], s - (q ? u4 : u2), acc);
             }
             lap += acc;
         }
-        const float c = sm[zl * SW + xc];
         gm[j] = p.gcoef * (layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2z);
         dv[j] = step_update(c, uu[j], kk[j], lap, gm[j], o[j]);
     }
@@ -305,7 +442,7 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
         });
     if (!live) return;
     *reinterpret_cast<float4 *>(p.u_prev + off) = un;
-    if (MODE == kModeStoreD)
+    if (MODE != kModeAdjoint && p.dseg_out)
         *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
     if (MODE == kModeAdjoint) {
         const float4 d = ldg4(p.dseg_in + off);
@@ -323,7 +460,7 @@ KernelFn pick_mode(int mode)
 {
     switch (mode) {
     case kModeForward: return step2d_kernel<SHAPE, M, 0, kModeForward, R>;
-    case kModeStoreD: return step2d_kernel<SHAPE, M, 0, kModeStoreD, R>;
+    case kModeStoreD: return step2d_kernel<SHAPE, M, 0, kModeForward, R>;
     default: return step2d_kernel<SHAPE, M, 0, kModeAdjoint, R>;
     }
 }
@@ -353,7 +490,47 @@ BatchFn lookup_batched(int shape, int M, int R)
     return nullptr;
 }
 
+using PersistFn = void (*)(const PersistParams);
+
+PersistFn lookup_persist(int shape, int M, int R)
+{
+#define FDW_P(S, MM, RR) \
+    if (shape == S && M == MM && R == RR) return step2d_persistent<S, MM, RR>;
+    FDW_P(FD_CROSS, 2, 1) FDW_P(FD_CROSS, 4, 1) FDW_P(FD_CROSS, 8, 1)
+    FDW_P(FD_CROSS, 2, 4) FDW_P(FD_CROSS, 4, 4) FDW_P(FD_CROSS, 8, 4)
+    FDW_P(FD_RHOMBUS, 2, 4) FDW_P(FD_RHOMBUS, 4, 4) FDW_P(FD_RHOMBUS, 8, 4)
+    FDW_P(FD_SQUARE, 2, 4) FDW_P(FD_SQUARE, 4, 4) FDW_P(FD_SQUARE, 8, 4)
+#undef FDW_P
+    return nullptr;
+}
+
 }  // namespace
+
+// Resident CTAs of the persistent 2D kernel for this variant (0: not available).
+int persist2d_grid(const Variant &v, int ntiles)
+{
+    PersistFn fn = lookup_persist(v.shape, v.M, v.tz / kTZ);
+    if (!fn || v.generic) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem) != cudaSuccess)
+        return 0;
+    int dev = 0, nsm = 0, per = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kThreads, v.smem) != cudaSuccess)
+        return 0;
+    const int g = per * nsm;
+    return g < ntiles ? g : ntiles;
+}
+
+cudaError_t launch_persist2d(const Variant &v, const PersistParams &pp, int grid, cudaStream_t s)
+{
+    PersistFn fn = lookup_persist(v.shape, v.M, v.tz / kTZ);
+    if (!fn) return cudaErrorInvalidValue;
+    void *args[] = {const_cast<PersistParams *>(&pp)};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(fn), dim3(grid), dim3(kThreads),
+                                       args, v.smem, s);
+}
 
 int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v)
 {
@@ -432,7 +609,7 @@ cudaError_t launch_step2d(const Variant &v, int mode, const StepParams &p, cudaS
     }
     void (*fn)(const StepParams, int, int, int) =
         mode == kModeForward ? step2d_generic<kModeForward>
-        : mode == kModeStoreD ? step2d_generic<kModeStoreD> : step2d_generic<kModeAdjoint>;
+        : mode == kModeStoreD ? step2d_generic<kModeForward> : step2d_generic<kModeAdjoint>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)v.smem);
     if (e != cudaSuccess) return e;

@@ -2,12 +2,14 @@
 // spacexz_derivative2_sym as the union of the 2D shape in the three coordinate
 // planes), fused with damping, injection, sampling and the FWI modes.
 //
-// A CTA owns a 64 x TY column of (x, y) and marches a chunk of z planes.  The
-// planes z-M .. z+M (plus prefetch) of the input field, each with an x halo
-// of round4(M) and a y halo of M, sit in a ring of shared-memory slots filled
-// by TMA (out-of-bounds zero fill = zero field outside the padded grid), one
-// mbarrier per slot.  Thread (tx, ty) owns 4 consecutive x (one float4) of
-// row y0 + ty in every plane of the chunk.
+// A CTA owns a 64 x TY column of (x, y) and marches a chunk of z planes.  A
+// producer warp streams the planes through a ring of shared-memory slots with
+// TMA (out-of-bounds zero fill = zero field outside the padded grid), one full
+// and one empty mbarrier per slot; the consumer threads (tx, ty) each own 4
+// consecutive x (one float4) of row y0 + ty in every plane of the chunk.  Two
+// kernels: step3d_cross (z arm in a register queue) and step3d_planar
+// (rhombus and square: each plane scattered into a register accumulator of the
+// outputs it touches).
 #include "device_common.cuh"
 
 namespace fdw {
@@ -15,10 +17,6 @@ namespace fdw {
 namespace {
 
 constexpr int kTX3 = 64;
-constexpr int kPF = 2;     // planes prefetched beyond the stencil's reach
-
-template <int M>
-constexpr int ring_slots() { return 2 * M + 1 + kPF; }
 
 // Tile table walk for one plane: apply f(j, entry) to owned entries with
 // entry.z == z; `k` advances past them (entries are z-sorted per tile).
@@ -60,214 +58,8 @@ __device__ __noinline__ int sample_plane(const StepParams &p, int &k, int kend, 
     return k < kend ? p.smp[k].z : 0x7fffffff;
 }
 
-template <int SHAPE, int M, int MODE, int TY>
-__global__ void __launch_bounds__(16 * TY) step3d_kernel(const __grid_constant__ StepParams p)
-{
-    constexpr int HX = round4(M);
-    constexpr int PW = kTX3 + 2 * HX;
-    constexpr int PH = TY + 2 * M;
-    constexpr int PLANE = PW * PH;          // floats copied per plane
-    constexpr int SLOT = (PLANE + 31) & ~31;  // slot stride: 128-byte aligned TMA destinations
-    constexpr int NS = ring_slots<M>();
-    extern __shared__ __align__(1024) float sm[];
-    __shared__ uint64_t bar[NS];
-
-    const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
-    const int ntile = p.tiles_x * p.tiles_y;
-    const int tile = blockIdx.x % ntile, zc = blockIdx.x / ntile;
-    const int x0 = (tile % p.tiles_x) * kTX3, y0 = (tile / p.tiles_x) * TY;
-    const int zb = zc * p.zchunk;
-    const int ze = min((int)p.nz, zb + p.zchunk);
-    const int L = (ze - zb) + 2 * M;
-
-    int issued = 0;
-    if (tid == 0) {
-        prefetch_tmap(p.tmap);
-        for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        for (; issued < NS && issued < L; ++issued) {
-            mbar_arrive_expect_tx(&bar[issued], PLANE * 4);
-            tma_load_3d(sm + issued * SLOT, p.tmap, &bar[issued], x0 - HX, y0 - M,
-                        zb - M + issued);
-        }
-    }
-
-    const int xg = x0 + 4 * tx, yg = y0 + ty;
-    const bool colok = xg < p.nx && yg < p.ny;
-    float d2xy[4];
-    {
-        const float d2y = layer_d2(yg, p.phys_lo[1], p.phys_hi[1]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) d2xy[j] = layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2y;
-    }
-    int ki = p.inj_ptr ? p.inj_ptr[tile] : 0, kie = p.inj_ptr ? p.inj_ptr[tile + 1] : 0;
-    int ks = p.smp_ptr ? p.smp_ptr[tile] : 0, kse = p.smp_ptr ? p.smp_ptr[tile + 1] : 0;
-
-    const int64_t colo = (int64_t)yg * p.pitch + xg;
-    float4 up_n = make_float4(0.f, 0.f, 0.f, 0.f), kp_n = up_n;
-    if (colok && zb < ze) {
-        up_n = ldg4(p.u_prev + (int64_t)zb * p.plane + colo);
-        kp_n = ldg4(p.kappa + (int64_t)zb * p.plane + colo);
-    }
-    bool ok = true;
-    for (int zi = 0; zi < ze - zb; ++zi) {
-        const int z = zb + zi;
-        const float4 up = up_n, kp = kp_n;
-        if (colok && zi + 1 < ze - zb) {
-            up_n = ldg4(p.u_prev + (int64_t)(z + 1) * p.plane + colo);
-            kp_n = ldg4(p.kappa + (int64_t)(z + 1) * p.plane + colo);
-        }
-        for (int i = (zi == 0 ? 0 : zi + 2 * M); i <= zi + 2 * M; ++i)
-            ok = ok && mbar_wait_bounded(&bar[i % NS], (i / NS) & 1);
-
-        float lap[4] = {0.f, 0.f, 0.f, 0.f};
-        const int yl = M + ty;
-        const float *P0 = sm + ((zi + M) % NS) * SLOT;
-        // in-plane (xy) part of the shape
-#pragma unroll
-        for (int q = 0; q <= M; ++q) {
-            const int E = shape_ext(SHAPE, M, 0, q);
-            const int E4 = round4(E);
-            float win[4 + 2 * HX];
-            const float *rp = P0 + (yl + q) * PW + HX + 4 * tx - E4;
-            const float *rm = P0 + (yl - q) * PW + HX + 4 * tx - E4;
-#pragma unroll
-            for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
-                float4 a = ld4(rp + 4 * i);
-                if (q > 0) {
-                    const float4 b = ld4(rm + 4 * i);
-                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-                }
-                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float acc = p.w[q] * win[E4 + j];
-#pragma unroll
-                for (int pp = 1; pp <= E; ++pp)
-                    acc = fmaf(p.w[pp * kWDim + q], win[E4 + j + pp] + win[E4 + j - pp], acc);
-                lap[j] += acc;
-            }
-        }
-        // planes z +- s: the xz-plane line (row y) and the yz-plane column
-#pragma unroll
-        for (int s = 1; s <= M; ++s) {
-            const int E = shape_ext(SHAPE, M, 0, s);
-            const int E4 = round4(E);
-            const float *Pp = sm + ((zi + M + s) % NS) * SLOT;
-            const float *Pm = sm + ((zi + M - s) % NS) * SLOT;
-            float win[4 + 2 * HX];
-            const float *rp = Pp + yl * PW + HX + 4 * tx - E4;
-            const float *rm = Pm + yl * PW + HX + 4 * tx - E4;
-#pragma unroll
-            for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
-                float4 a = ld4(rp + 4 * i);
-                const float4 b = ld4(rm + 4 * i);
-                a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float acc = p.w[s] * win[E4 + j];
-#pragma unroll
-                for (int pp = 1; pp <= E; ++pp)
-                    acc = fmaf(p.w[pp * kWDim + s], win[E4 + j + pp] + win[E4 + j - pp], acc);
-                lap[j] += acc;
-            }
-#pragma unroll
-            for (int qq = 1; qq <= E; ++qq) {
-                const int c = HX + 4 * tx;
-                float4 a = ld4(Pp + (yl + qq) * PW + c);
-                const float4 b = ld4(Pp + (yl - qq) * PW + c);
-                const float4 d = ld4(Pm + (yl + qq) * PW + c);
-                const float4 e = ld4(Pm + (yl - qq) * PW + c);
-                const float wq = p.w[qq * kWDim + s];
-                lap[0] = fmaf(wq, (a.x + b.x) + (d.x + e.x), lap[0]);
-                lap[1] = fmaf(wq, (a.y + b.y) + (d.y + e.y), lap[1]);
-                lap[2] = fmaf(wq, (a.z + b.z) + (d.z + e.z), lap[2]);
-                lap[3] = fmaf(wq, (a.w + b.w) + (d.w + e.w), lap[3]);
-            }
-        }
-
-        const float4 c = ld4(P0 + yl * PW + HX + 4 * tx);
-        const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
-        const float cc[4] = {c.x, c.y, c.z, c.w};
-        const float uu[4] = {up.x, up.y, up.z, up.w};
-        const float kk[4] = {kp.x, kp.y, kp.z, kp.w};
-        float o[4], dv[4], g[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            g[j] = p.gcoef * (d2xy[j] + d2z);
-            dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
-        }
-        if (p.inj_ptr)
-            plane_entries(p.inj, ki, kie, z, tx, ty, [&](int j, const PtEntry &en) {
-                float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
-                if (MODE == kModeAdjoint) a *= kk[j];
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
-                    if (jj == j) o[jj] += a;
-            });
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
-        if (p.smp_ptr)
-            plane_entries(p.smp, ks, kse, z, tx, ty, [&](int j, const PtEntry &en) {
-                float v = 0.f;
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
-                    if (jj == j) v = o[jj];
-                v *= en.scale;
-                if (MODE == kModeAdjoint) v /= kk[j];
-                p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
-            });
-        if (colok) {
-            const int64_t off = (int64_t)z * p.plane + colo;
-            const float4 un = make_float4(o[0], o[1], o[2], o[3]);
-            *reinterpret_cast<float4 *>(p.u_prev + off) = un;
-            if (MODE == kModeStoreD)
-                *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
-            if (MODE == kModeAdjoint) {
-                const float4 d = ldg4(p.dseg_in + off);
-                float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
-                ga.x = fmaf(un.x, d.x, ga.x); ga.y = fmaf(un.y, d.y, ga.y);
-                ga.z = fmaf(un.z, d.z, ga.z); ga.w = fmaf(un.w, d.w, ga.w);
-                *reinterpret_cast<float4 *>(p.gacc + off) = ga;
-            }
-        }
-        // all threads are done with plane zi - M (slot zi % NS): refill it
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(p.status, kStatusTimeout);
-                for (int i = zi + 2 * M + 1; i < issued; ++i)
-                    mbar_wait_bounded(&bar[i % NS], (i / NS) & 1, 100000000LL);
-            }
-            return;
-        }
-        if (tid == 0 && issued < L) {
-            const int slot = issued % NS;
-            mbar_arrive_expect_tx(&bar[slot], PLANE * 4);
-            tma_load_3d(sm + slot * SLOT, p.tmap, &bar[slot], x0 - HX, y0 - M, zb - M + issued);
-            ++issued;
-        }
-    }
-}
-
 using KernelFn = void (*)(const StepParams);
 
-template <int SHAPE, int M, int TY>
-KernelFn pick3(int mode)
-{
-    switch (mode) {
-    case kModeForward: return step3d_kernel<SHAPE, M, kModeForward, TY>;
-    case kModeStoreD: return step3d_kernel<SHAPE, M, kModeStoreD, TY>;
-    default: return step3d_kernel<SHAPE, M, kModeAdjoint, TY>;
-    }
-}
 
 
 // ---------------------------------------------------------------------------
@@ -431,17 +223,14 @@ step3d_cross(const __grid_constant__ StepParams p)
                     const float4 a = ld4(P + cA - HX + 4 * i);
                     win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
                 }
-                float lx[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float acc = p.w[0] * win[HX + j];
-#pragma unroll
-                    for (int m = 1; m <= M; ++m)
-                        acc = fmaf(p.w[m * kWDim], win[HX + j + m] + win[HX + j - m], acc);
-                    lx[j] = acc;
-                }
-                f32x2 l01 = pk2(lx[0], lx[1]), l23 = pk2(lx[2], lx[3]);
-                // y and z arms: W[0][m] (u(y+m) + u(y-m) + u(z+m) + u(z-m)), two lanes per op
+                // centre-free Laplacian: W[0][m] ((sum of the 6 points at distance
+                // m) - 6 u), the six summed as x pair + (y pair + z pair) so that a
+                // constant field gives 6u rounded exactly like the 6u subtracted
+                const f32x2 c01 = pk2(win[HX], win[HX + 1]), c23 = pk2(win[HX + 2], win[HX + 3]);
+                const f32x2 u2_01 = add2(c01, c01), u2_23 = add2(c23, c23);
+                const f32x2 u6_01 = add2(u2_01, add2(u2_01, u2_01));
+                const f32x2 u6_23 = add2(u2_23, add2(u2_23, u2_23));
+                f32x2 l01 = 0ull, l23 = 0ull;
 #pragma unroll
                 for (int m = 1; m <= M; ++m) {
                     f32x2 a01, a23, b01, b23;
@@ -449,8 +238,12 @@ step3d_cross(const __grid_constant__ StepParams p)
                     ld4x2(P + cA - m * PW, b01, b23);
                     const int ip = (u - M + m + 2 * QL) % QL, im = (u - M - m + 2 * QL) % QL;
                     const f32x2 wm = pk2(p.w[m], p.w[m]);
-                    l01 = fma2(wm, add2(add2(a01, b01), add2(qa[ip], qa[im])), l01);
-                    l23 = fma2(wm, add2(add2(a23, b23), add2(qb[ip], qb[im])), l23);
+                    const f32x2 x01 = pk2(win[HX + m] + win[HX - m], win[HX + 1 + m] + win[HX + 1 - m]);
+                    const f32x2 x23 = pk2(win[HX + 2 + m] + win[HX + 2 - m], win[HX + 3 + m] + win[HX + 3 - m]);
+                    const f32x2 s01 = add2(x01, add2(add2(a01, b01), add2(qa[ip], qa[im])));
+                    const f32x2 s23 = add2(x23, add2(add2(a23, b23), add2(qb[ip], qb[im])));
+                    l01 = fma2(wm, sub2(s01, u6_01), l01);
+                    l23 = fma2(wm, sub2(s23, u6_23), l23);
                 }
                 f32x2 up01, up23, k01, k23;
                 ld4x2(P + C::AEL + cT, up01, up23);
@@ -482,7 +275,7 @@ step3d_cross(const __grid_constant__ StepParams p)
                 if (colok) {
                     const int64_t off = (int64_t)z * p.plane + colo;
                     *reinterpret_cast<float4 *>(p.u_prev + off) = o;
-                    if (MODE == kModeStoreD)
+                    if (MODE != kModeAdjoint && p.dseg_out)
                         *reinterpret_cast<ulonglong2 *>(p.dseg_out + off) = make_ulonglong2(dv01, dv23);
                     if (MODE == kModeAdjoint) {
                         const float4 dd = ldg4(p.dseg_in + off);
@@ -608,151 +401,180 @@ step3d_planar(const __grid_constant__ StepParams p)
     const int cA = (M + ty) * PW + HX + 4 * tx;
     const int cT = ty * kTX3 + 4 * tx;
 
+    int zinj = ki < kie ? p.inj[ki].z : 0x7fffffff;
+    int zsmp = ks < kse ? p.smp[ks].z : 0x7fffffff;
+    // acc[i] holds output P - M + i after the shift at plane P (i = 0..2M); the
+    // accumulators move down one slot per plane (no unroll: small code)
     float4 acc[QL];
 #pragma unroll
     for (int i = 0; i < QL; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // centre values of the previous plane; the first plane's step only feeds
+    // outputs below the chunk, so its start value does not matter
+    f32x2 cprev01 = 0ull, cprev23 = 0ull;
     int slot = 0;
     uint32_t fph = 0;
     bool ok = true;
 
-    // output o accumulates in slot (o - zb + M) mod QL; at stream index t (plane
-    // P = zb - M + t, t = t0 + u with t0 a multiple of QL) output P + s is slot (u + s) mod QL
-    for (int t0 = 0; t0 < S; t0 += QL) {
+    for (int t = 0; t < S; ++t) {
+        ok = ok && mbar_wait_bounded(&full[slot], fph);
+        if (!ok) break;
+        const float *A = sm + slot * SLOT;
 #pragma unroll
-        for (int u = 0; u < QL; ++u) {
-            const int t = t0 + u;
-            if (t >= S) break;
-            ok = ok && mbar_wait_bounded(&full[slot], fph);
-            if (!ok) break;
-            const float *A = sm + slot * SLOT;
-            acc[(u + M) % QL] = make_float4(0.f, 0.f, 0.f, 0.f);   // output P + M starts here
-            float T[M + 1][4];
+        for (int i = 0; i < QL - 1; ++i) acc[i] = acc[i + 1];
+        acc[QL - 1] = make_float4(0.f, 0.f, 0.f, 0.f);       // output P + M starts here
+        // Centre-free Laplacian, split per plane: T[s] sums the points of plane
+        // P at |dz| = s minus plane P's own centre value c(P) (n points, n c(P)
+        // subtracted before weighting); the z-axis remainder
+        // sum_s A_s (c(z+s) + c(z-s) - 2 c(z)), A_s the total weight at |dz| = s,
+        // is telescoped into plane-to-plane steps dl(P) = c(P) - c(P-1):
+        // output P - s gets +B_s dl(P) (s >= 1) and output P + s gets
+        // -B_{s+1} dl(P) (s >= 0), B_i = sum_{s >= i} A_s.  A constant field
+        // gives exactly zero, and every accumulated term is a small difference.
+        float T[M + 1][4];
 #pragma unroll
-            for (int s = 0; s <= M; ++s)
+        for (int s = 0; s <= M; ++s)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) T[s][j] = 0.f;
-            {   // row y of P: centre, in-plane x line (s = 0) and xz lines (s >= 1)
-                float win[4 + 2 * HX];
+            for (int j = 0; j < 4; ++j) T[s][j] = 0.f;
+        float u2[4], u4[4];
+        f32x2 dl01, dl23;
+        {   // row y of P: in-plane x line (s = 0) and xz lines (s >= 1)
+            float win[4 + 2 * HX];
 #pragma unroll
-                for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
-                    const float4 a = ld4(A + cA - HX + 4 * i);
-                    win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float ps[M + 1];
-#pragma unroll
-                    for (int pp = 1; pp <= M; ++pp) ps[pp] = win[HX + j + pp] + win[HX + j - pp];
-#pragma unroll
-                    for (int s = 0; s <= M; ++s) {
-                        const int E = shape_ext(SHAPE, M, 0, s);
-                        float a = p.w[s] * win[HX + j];
-#pragma unroll
-                        for (int pp = 1; pp <= E; ++pp) a = fmaf(p.w[pp * kWDim + s], ps[pp], a);
-                        T[s][j] += a;
-                    }
-                }
+            for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
+                const float4 a = ld4(A + cA - HX + 4 * i);
+                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
             }
+            const f32x2 c01 = pk2(win[HX], win[HX + 1]), c23 = pk2(win[HX + 2], win[HX + 3]);
+            dl01 = sub2(c01, cprev01);
+            dl23 = sub2(c23, cprev23);
+            cprev01 = c01;
+            cprev23 = c23;
 #pragma unroll
-            for (int q = 1; q <= M; ++q) {   // row pairs y +- q: in-plane rows and yz columns
-                const int E = shape_ext(SHAPE, M, 0, q);
-                const int E4 = round4(E);
-                float win[4 + 2 * HX];
-                const float *rp = A + cA + q * PW - E4;
-                const float *rm = A + cA - q * PW - E4;
+            for (int j = 0; j < 4; ++j) {
+                u2[j] = win[HX + j] + win[HX + j];
+                u4[j] = u2[j] + u2[j];
+                float ps[M + 1];
 #pragma unroll
-                for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
-                    float4 a = ld4(rp + 4 * i);
-                    const float4 b = ld4(rm + 4 * i);
-                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-                    win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+                for (int pp = 1; pp <= M; ++pp) ps[pp] = (win[HX + j + pp] + win[HX + j - pp]) - u2[j];
+#pragma unroll
+                for (int s = 0; s <= M; ++s) {
+                    const int E = shape_ext(SHAPE, M, 0, s);
+                    if (E < 1) continue;
+                    float a = p.w[kWDim + s] * ps[1];
+#pragma unroll
+                    for (int pp = 2; pp <= E; ++pp) a = fmaf(p.w[pp * kWDim + s], ps[pp], a);
+                    T[s][j] = a;
                 }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float a = p.w[q] * win[E4 + j];
-#pragma unroll
-                    for (int pp = 1; pp <= E; ++pp)
-                        a = fmaf(p.w[pp * kWDim + q], win[E4 + j + pp] + win[E4 + j - pp], a);
-                    T[0][j] += a;
-#pragma unroll
-                    for (int s = 1; s <= M; ++s)
-                        if (q <= shape_ext(SHAPE, M, 0, s)) T[s][j] = fmaf(p.w[q * kWDim + s], win[E4 + j], T[s][j]);
-                }
-            }
-            float4 cv = make_float4(0.f, 0.f, 0.f, 0.f), upv = cv, kpv = cv;
-            const bool fin = t >= 2 * M;
-            if (fin) {
-                cv = ld4(A + C::AEL + cT);
-                upv = ld4(A + C::AEL + C::TEL + cT);
-                kpv = ld4(A + C::AEL + 2 * C::TEL + cT);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[slot]);
-            // scatter: T[0] -> output P, T[s] -> outputs P - s and P + s
-            acc[u].x += T[0][0]; acc[u].y += T[0][1]; acc[u].z += T[0][2]; acc[u].w += T[0][3];
-#pragma unroll
-            for (int s = 1; s <= M; ++s) {
-                float4 &ap = acc[(u + s) % QL];
-                float4 &am = acc[(u - s + QL) % QL];
-                ap.x += T[s][0]; ap.y += T[s][1]; ap.z += T[s][2]; ap.w += T[s][3];
-                am.x += T[s][0]; am.y += T[s][1]; am.z += T[s][2]; am.w += T[s][3];
-            }
-            if (fin) {   // output z = P - M is complete
-                const int z = zb + t - 2 * M;
-                const float4 lv = acc[(u - M + QL) % QL];
-                const float lap[4] = {lv.x, lv.y, lv.z, lv.w};
-                const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
-                const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
-                const float uu[4] = {upv.x, upv.y, upv.z, upv.w};
-                const float kk[4] = {kpv.x, kpv.y, kpv.z, kpv.w};
-                float o[4], dv[4], g[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    g[j] = p.gcoef * (d2xy[j] + d2z);
-                    dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
-                }
-                if (p.inj_ptr)
-                    plane_entries(p.inj, ki, kie, z, tx, ty, [&](int j, const PtEntry &en) {
-                        float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
-                        if (MODE == kModeAdjoint) a *= kk[j];
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj)
-                            if (jj == j) o[jj] += a;
-                    });
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
-                if (p.smp_ptr)
-                    plane_entries(p.smp, ks, kse, z, tx, ty, [&](int j, const PtEntry &en) {
-                        float v = 0.f;
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj)
-                            if (jj == j) v = o[jj];
-                        v *= en.scale;
-                        if (MODE == kModeAdjoint) v /= kk[j];
-                        p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
-                    });
-                if (colok) {
-                    const int64_t off = (int64_t)z * p.plane + colo;
-                    const float4 un = make_float4(o[0], o[1], o[2], o[3]);
-                    *reinterpret_cast<float4 *>(p.u_prev + off) = un;
-                    if (MODE == kModeStoreD)
-                        *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
-                    if (MODE == kModeAdjoint) {
-                        const float4 dd = ldg4(p.dseg_in + off);
-                        float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
-                        ga.x = fmaf(un.x, dd.x, ga.x); ga.y = fmaf(un.y, dd.y, ga.y);
-                        ga.z = fmaf(un.z, dd.z, ga.z); ga.w = fmaf(un.w, dd.w, ga.w);
-                        *reinterpret_cast<float4 *>(p.gacc + off) = ga;
-                    }
-                }
-            }
-            if (++slot == NR) {
-                slot = 0;
-                fph ^= 1u;
             }
         }
-        if (!ok) break;
+#pragma unroll
+        for (int q = 1; q <= M; ++q) {   // row pairs y +- q: in-plane rows and yz columns
+            const int E = shape_ext(SHAPE, M, 0, q);
+            const int E4 = round4(E);
+            float win[4 + 2 * HX];
+            const float *rp = A + cA + q * PW - E4;
+            const float *rm = A + cA - q * PW - E4;
+#pragma unroll
+            for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
+                float4 a = ld4(rp + 4 * i);
+                const float4 b = ld4(rm + 4 * i);
+                a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float d0 = win[E4 + j] - u2[j];
+                float a = p.w[q] * d0;
+#pragma unroll
+                for (int pp = 1; pp <= E; ++pp)
+                    a = fmaf(p.w[pp * kWDim + q], (win[E4 + j + pp] + win[E4 + j - pp]) - u4[j], a);
+                T[0][j] += a;
+#pragma unroll
+                for (int s = 1; s <= M; ++s)
+                    if (q <= shape_ext(SHAPE, M, 0, s)) T[s][j] = fmaf(p.w[q * kWDim + s], d0, T[s][j]);
+            }
+        }
+        float4 cv = make_float4(0.f, 0.f, 0.f, 0.f), upv = cv, kpv = cv;
+        const bool fin = t >= 2 * M;
+        if (fin) {
+            cv = ld4(A + C::AEL + cT);
+            upv = ld4(A + C::AEL + C::TEL + cT);
+            kpv = ld4(A + C::AEL + 2 * C::TEL + cT);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (++slot == NR) {
+            slot = 0;
+            fph ^= 1u;
+        }
+        // scatter: T[0] - B_1 dl -> output P (slot M); T[s] + B_s dl -> output
+        // P - s; T[s] - B_{s+1} dl -> output P + s
+        {
+            f32x2 a01, a23;
+            const f32x2 nb1 = pk2(-p.zarm[1], -p.zarm[1]);
+            f32x2 t01 = fma2(nb1, dl01, pk2(T[0][0], T[0][1]));
+            f32x2 t23 = fma2(nb1, dl23, pk2(T[0][2], T[0][3]));
+            a01 = add2(pk2(acc[M].x, acc[M].y), t01);
+            a23 = add2(pk2(acc[M].z, acc[M].w), t23);
+            upk2(a01, acc[M].x, acc[M].y);
+            upk2(a23, acc[M].z, acc[M].w);
+#pragma unroll
+            for (int s = 1; s <= M; ++s) {
+                const f32x2 ts01 = pk2(T[s][0], T[s][1]), ts23 = pk2(T[s][2], T[s][3]);
+                const f32x2 bm = pk2(p.zarm[s], p.zarm[s]);
+                float4 &am = acc[M - s];
+                t01 = fma2(bm, dl01, ts01);
+                t23 = fma2(bm, dl23, ts23);
+                a01 = add2(pk2(am.x, am.y), t01); upk2(a01, am.x, am.y);
+                a23 = add2(pk2(am.z, am.w), t23); upk2(a23, am.z, am.w);
+                float4 &ap = acc[M + s];
+                if (s < M) {
+                    const f32x2 bp = pk2(-p.zarm[s + 1], -p.zarm[s + 1]);
+                    t01 = fma2(bp, dl01, ts01);
+                    t23 = fma2(bp, dl23, ts23);
+                } else {
+                    t01 = ts01;
+                    t23 = ts23;
+                }
+                a01 = add2(pk2(ap.x, ap.y), t01); upk2(a01, ap.x, ap.y);
+                a23 = add2(pk2(ap.z, ap.w), t23); upk2(a23, ap.z, ap.w);
+            }
+        }
+        if (!fin) continue;
+        const int z = zb + t - 2 * M;             // output z = P - M is complete (slot 0)
+        const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
+        float g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) g[j] = p.gcoef * (d2xy[j] + d2z);
+        f32x2 o01, o23;
+        const f32x2 dv01 = step_update2(pk2(cv.x, cv.y), pk2(upv.x, upv.y), pk2(kpv.x, kpv.y),
+                                        pk2(acc[0].x, acc[0].y), pk2(g[0], g[1]), o01);
+        const f32x2 dv23 = step_update2(pk2(cv.z, cv.w), pk2(upv.z, upv.w), pk2(kpv.z, kpv.w),
+                                        pk2(acc[0].z, acc[0].w), pk2(g[2], g[3]), o23);
+        float4 o;
+        upk2(o01, o.x, o.y);
+        upk2(o23, o.z, o.w);
+        if (z >= zinj) zinj = inject_plane<MODE>(p, ki, kie, z, tx, ty, o, kpv);
+        if (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f || g[3] != 0.f) {
+            o.x = g[0] != 0.f ? __fdividef(o.x, 1.f + g[0]) : o.x;
+            o.y = g[1] != 0.f ? __fdividef(o.y, 1.f + g[1]) : o.y;
+            o.z = g[2] != 0.f ? __fdividef(o.z, 1.f + g[2]) : o.z;
+            o.w = g[3] != 0.f ? __fdividef(o.w, 1.f + g[3]) : o.w;
+        }
+        if (z >= zsmp) zsmp = sample_plane<MODE>(p, ks, kse, z, tx, ty, o, kpv);
+        if (colok) {
+            const int64_t off = (int64_t)z * p.plane + colo;
+            *reinterpret_cast<float4 *>(p.u_prev + off) = o;
+            if (MODE != kModeAdjoint && p.dseg_out)
+                *reinterpret_cast<ulonglong2 *>(p.dseg_out + off) = make_ulonglong2(dv01, dv23);
+            if (MODE == kModeAdjoint) {
+                const float4 dd = ldg4(p.dseg_in + off);
+                float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
+                ga.x = fmaf(o.x, dd.x, ga.x); ga.y = fmaf(o.y, dd.y, ga.y);
+                ga.z = fmaf(o.z, dd.z, ga.z); ga.w = fmaf(o.w, dd.w, ga.w);
+                *reinterpret_cast<float4 *>(p.gacc + off) = ga;
+            }
+        }
     }
     if (!ok) {
         atomicOr(p.status, kStatusTimeout);
@@ -765,7 +587,7 @@ KernelFn pick_planar(int mode)
 {
     switch (mode) {
     case kModeForward: return step3d_planar<SHAPE, M, kModeForward, TY>;
-    case kModeStoreD: return step3d_planar<SHAPE, M, kModeStoreD, TY>;
+    case kModeStoreD: return step3d_planar<SHAPE, M, kModeForward, TY>;
     default: return step3d_planar<SHAPE, M, kModeAdjoint, TY>;
     }
 }
@@ -775,7 +597,7 @@ KernelFn pick_cross(int mode)
 {
     switch (mode) {
     case kModeForward: return step3d_cross<M, kModeForward, TY>;
-    case kModeStoreD: return step3d_cross<M, kModeStoreD, TY>;
+    case kModeStoreD: return step3d_cross<M, kModeForward, TY>;
     default: return step3d_cross<M, kModeAdjoint, TY>;
     }
 }
@@ -793,13 +615,6 @@ KernelFn lookup3(int shape, int M, int ty, int mode)
     FDW_P(FD_RHOMBUS, 6, 8) FDW_P(FD_RHOMBUS, 8, 8) FDW_P(FD_SQUARE, 2, 16) FDW_P(FD_SQUARE, 4, 16)
     FDW_P(FD_RHOMBUS, 4, 8)
 #undef FDW_P
-    return nullptr;
-#define FDW_C(S, MM, TT) \
-    if (shape == S && M == MM && ty == TT) return pick3<S, MM, TT>(mode);
-    FDW_C(FD_RHOMBUS, 2, 16) FDW_C(FD_RHOMBUS, 3, 16) FDW_C(FD_RHOMBUS, 4, 16)
-    FDW_C(FD_RHOMBUS, 6, 8) FDW_C(FD_RHOMBUS, 8, 8)
-    FDW_C(FD_SQUARE, 2, 16) FDW_C(FD_SQUARE, 4, 16)
-#undef FDW_C
     return nullptr;
 }
 
@@ -822,7 +637,6 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
     v->box[0] = kTX3 + 2 * HX;
     v->box[1] = ty + 2 * M;
     v->box[2] = 1;
-    v->smem = (size_t)(2 * M + 1 + kPF) * ((v->box[0] * v->box[1] + 31) & ~31) * sizeof(float);
     v->tbox[0] = kTX3;
     v->tbox[1] = ty;
     {   // warp-specialised pipelines (cross and planar): one extra producer warp

@@ -156,3 +156,63 @@ def test_autotune_keeps_results_bitwise(dim, shape, M, scheme):
     p2 = c.plan()
     p2.autotune(torch.from_numpy(c.vel).cuda())
     assert tuple(p2.info().tile) == tuple(after.tile)
+
+
+def test_time_loop_schedules_are_bitwise_equal(monkeypatch):
+    """The time loop runs as a captured CUDA graph (default, replayed on repeat
+    calls), as plain launches, or as one persistent cooperative launch (opt-in
+    for small 2D grids); all three give bitwise identical results."""
+    c = _case2d("rhombus", 4, 0, "displs", nz=300, nx=280, nt=200)
+    tr_g, st_g, rc = c.gpu_forward()
+    assert rc == 0
+    tr_g2, st_g2, _ = c.gpu_forward()
+    monkeypatch.setenv("FDWAVE_GRAPHS", "0")
+    tr_s, st_s, rc = c.gpu_forward()
+    assert rc == 0
+    monkeypatch.setenv("FDWAVE_PERSISTENT", "1")
+    tr_p, st_p, rc = c.gpu_forward()
+    assert rc == 0
+    for tr, st in ((tr_g2, st_g2), (tr_s, st_s), (tr_p, st_p)):
+        assert np.array_equal(tr, tr_g) and np.array_equal(st, st_g)
+
+
+def test_graph_cache_survives_plan_and_buffer_reuse(monkeypatch):
+    """Plans and tensors freed and re-created at recycled addresses with a
+    different stencil must not replay another plan's captured time loop: the
+    graph cache is keyed by plan ids, never by addresses."""
+    runs = [("cross", 2, "spatte"), ("cross", 4, "spatte"), ("rhombus", 4, "displs"),
+            ("cross", 2, "spatte"), ("square", 2, "displs")]
+    got = []
+    for shape, M, scheme in runs:
+        c = _case2d(shape, M, 0, scheme, nz=90, nx=100, nt=40)
+        got.append(c.gpu_forward())
+    monkeypatch.setenv("FDWAVE_GRAPHS", "0")
+    for (shape, M, scheme), (tr, st, rc) in zip(runs, got):
+        c = _case2d(shape, M, 0, scheme, nz=90, nx=100, nt=40)
+        tr0, st0, rc0 = c.gpu_forward()
+        assert rc == 0 and rc0 == 0
+        assert np.array_equal(tr, tr0) and np.array_equal(st, st0), (shape, M, scheme)
+
+
+@pytest.mark.parametrize("dim,shape,M,N,scheme", [
+    (2, "cross", 4, 0, "spatte"), (2, "rhombus", 4, 0, "displs"), (2, "square", 8, 0, "displs"),
+    (2, "cross_rhombus", 4, 2, "dispte"), (2, "cross", 3, 0, "dispte"),
+    (3, "cross", 4, 0, "spatte"), (3, "cross", 8, 0, "spatte"), (3, "rhombus", 4, 0, "displs"),
+    (3, "square", 2, 0, "displs"),
+])
+def test_constant_field_is_a_fixed_point(dim, shape, M, N, scheme):
+    """A constant field (u^n = u^{n-1} = c) is an exact fixed point of one step
+    wherever the whole stencil lies in the grid and there is no sponge: the
+    kernels sum a_o (u(x+o) - u(x)), which is exactly zero there whatever the
+    FP32 rounding of the weights (a literal sum of a_o u(x+o) leaves
+    c * sum_o fl(a_o) != 0)."""
+    n = (40, 52) if dim == 2 else (24, 28, 36)
+    nb = 8
+    vel = smooth_velocity(n, 4, 1500.0, 3000.0, sigma=3.0)
+    c = Case(vel, 10.0, 1, nb, 3000.0, shape, M, N, scheme, src=np.zeros((0, dim)), rec=None)
+    pshape = tuple(s + 2 * nb for s in n)
+    st0 = np.full((2,) + pshape, 0.3712, np.float32)
+    _, st, rc = c.gpu_forward(state_in=st0)
+    assert rc == 0
+    inner = (slice(None),) + tuple(slice(nb, nb + s) for s in n)
+    assert np.array_equal(st[inner][0], st0[inner][0])
