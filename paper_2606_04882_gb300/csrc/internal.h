@@ -13,6 +13,8 @@ namespace fdw {
 
 constexpr int kMaxM = 16;                    // largest radius of any kernel
 constexpr int kWDim = kMaxM + 1;             // weight table is W[p][q], p,q in [0, M]
+constexpr int kMax3 = 8;                      // largest 3D radius
+constexpr int kW3 = kMax3 + 1;
 constexpr int kStatusTimeout = 1;            // status word bits
 constexpr int kStatusVmax = 2;
 
@@ -68,14 +70,19 @@ struct StepParams {
     float *gacc;               // kModeAdjoint: accumulator (same layout as fields)
     int *status;
     float w[kWDim * kWDim];    // symmetric weight table W[p][q] = a_orbit(max, min)
-    // 3D planar kernels: zarm[i] = sum_{s >= i} A_s, A_s the total weight of
-    // the points at |dz| = s (zarm[M + 1] = 0)
-    float zarm[kWDim];
+    // 3D kernels (M <= kMax3): the same weights as lane pairs (w, w) for packed
+    // FP32x2 arithmetic, W2[p * kW3 + q] = (W[p][q], W[p][q]); and for the
+    // planar kernels zp2[i] = (B_i, B_i), zm2[i] = (-B_{i+1}, -B_{i+1}) with
+    // B_i = sum_{s >= i} A_s, A_s the total weight of the points at |dz| = s
+    // (B_{M+1} = 0)
+    unsigned long long w2[kW3 * kW3];
+    unsigned long long zp2[kW3 + 1];
+    unsigned long long zm2[kW3 + 1];
 };
 
-// Batched 2D shots: per-shot descriptor in device memory (64-byte aligned for
-// the tensor maps) and the launch parameters of one time step.
-struct alignas(64) ShotDesc {
+// Batched 2D shots: per-shot descriptor in device memory (128-byte aligned, as
+// CUtensorMap is) and the launch parameters of one time step.
+struct alignas(128) ShotDesc {
     CUtensorMap tmap[2];       // halo-box maps of field buffers 0 and 1
     float *buf[2];             // buffer 0 holds u^0 at the start, buffer 1 u^{-1}
     const float *kappa;

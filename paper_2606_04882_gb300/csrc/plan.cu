@@ -266,19 +266,27 @@ void fill_params(const fd_plan *p, StepParams &sp)
     sp.zchunk = p->zchunk;
     sp.nz_chunks = p->nz_chunks;
     std::memcpy(sp.w, p->W, sizeof sp.w);
-    // z-axis weight sums of the planar 3D kernels, from the FP32 table
+    // packed 3D weight tables, from the FP32 table
+    auto pair = [](float v) {
+        uint32_t b;
+        std::memcpy(&b, &v, 4);
+        return ((unsigned long long)b << 32) | b;
+    };
+    for (int a = 0; a < kW3; ++a)
+        for (int c = 0; c < kW3; ++c) sp.w2[a * kW3 + c] = pair(p->W[a * kWDim + c]);
     const int M = p->st.M;
-    double A[kWDim + 1] = {0.0};
-    for (int s = 1; s <= M && s < kWDim; ++s) {
+    double A[kW3 + 1] = {0.0};
+    for (int s = 1; s <= M && s < kW3; ++s) {
         const int E = shape_ext(p->shape_eff, M, 0, s);
         double a = p->W[s];
         for (int pp = 1; pp <= E; ++pp) a += 4.0 * p->W[pp * kWDim + s];
         A[s] = a;
     }
     double B = 0.0;
-    for (int i = std::min(M, kWDim - 1); i >= 1; --i) {
+    for (int i = std::min(M, kW3 - 1); i >= 1; --i) {
         B += A[i];
-        sp.zarm[i] = (float)B;
+        sp.zp2[i] = pair((float)B);
+        sp.zm2[i - 1] = pair(-(float)B);
     }
 }
 

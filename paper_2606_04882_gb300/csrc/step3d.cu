@@ -33,29 +33,40 @@ __device__ __forceinline__ void plane_entries(const PtEntry *tab, int &k, int ke
 }
 
 // Out-of-line handlers for the (rare) planes that carry table entries, so the
-// unrolled plane loops stay small.  Return the z of the next pending entry.
+// unrolled plane loops stay small.  Everything goes in and out by value (a
+// reference would force the caller's registers into local memory every
+// plane); they return the next pending entry and its z.
+struct InjOut {
+    float4 o;
+    int k, z;
+};
+
 template <int MODE>
-__device__ __noinline__ int inject_plane(const StepParams &p, int &k, int kend, int z, int tx,
-                                         int ty, float4 &o, const float4 &kk)
+__device__ __noinline__ InjOut inject_plane(const StepParams &p, int k, int kend, int z, int tx,
+                                            int ty, float4 o, float4 kk)
 {
     plane_entries(p.inj, k, kend, z, tx, ty, [&](int j, const PtEntry &en) {
         float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
         if (MODE == kModeAdjoint) a *= get4(kk, j);
         add4(o, j, a);
     });
-    return k < kend ? p.inj[k].z : 0x7fffffff;
+    InjOut r;
+    r.o = o;
+    r.k = k;
+    r.z = k < kend ? p.inj[k].z : 0x7fffffff;
+    return r;
 }
 
 template <int MODE>
-__device__ __noinline__ int sample_plane(const StepParams &p, int &k, int kend, int z, int tx,
-                                         int ty, const float4 &o, const float4 &kk)
+__device__ __noinline__ int2 sample_plane(const StepParams &p, int k, int kend, int z, int tx,
+                                          int ty, float4 o, float4 kk)
 {
     plane_entries(p.smp, k, kend, z, tx, ty, [&](int j, const PtEntry &en) {
         float v = get4(o, j) * en.scale;
         if (MODE == kModeAdjoint) v /= get4(kk, j);
         p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
     });
-    return k < kend ? p.smp[k].z : 0x7fffffff;
+    return make_int2(k, k < kend ? p.smp[k].z : 0x7fffffff);
 }
 
 using KernelFn = void (*)(const StepParams);
@@ -183,40 +194,41 @@ step3d_cross(const __grid_constant__ StepParams p)
     const int cA = (M + ty) * PW + HX + 4 * tx;        // my centre in the halo plane
     const int cT = ty * kTX3 + 4 * tx;                 // my element in a tile
 
-    // queue of centre values as packed pairs (x, y) and (z, w)
-    f32x2 qa[QL], qb[QL];
+    // Queue of centre values as packed pairs (x, y) and (z, w).  Unrolled
+    // (M <= 4): the plane fed at stream index s sits in slot s mod QL and the
+    // loop is unrolled by QL.  Blocked (M >= 6, to keep the code small): the
+    // loop is unrolled by UF = 4 over a queue of QL + 3 slots that moves down
+    // UF slots at the start of each block; sub-step uu feeds slot QL-1+uu.
+    constexpr bool kUnroll = M <= 4;
+    constexpr int UF = kUnroll ? QL : 4;
+    constexpr int QN = kUnroll ? QL : QL + UF - 1;
+    f32x2 qa[QN], qb[QN];
 #pragma unroll
-    for (int i = 0; i < QL; ++i) qa[i] = qb[i] = 0ull;
+    for (int i = 0; i < QN; ++i) qa[i] = qb[i] = 0ull;
     int slot = 0;
     uint32_t fph = 0;
     bool ok = true;
 
-    // Queue addressing: unrolled (M <= 4), the plane fed at stream index s sits
-    // in slot s mod QL and the loop is unrolled by QL; shifted (M >= 6, to keep
-    // the code small), slot QL-1 always holds the newest plane and the queue
-    // moves down one slot per plane.
-    constexpr bool kUnroll = M <= 4;
-    constexpr int UF = kUnroll ? QL : 1;
     for (int k0 = 0; k0 < S; k0 += UF) {
+        if (!kUnroll) {
+#pragma unroll
+            for (int i = 0; i < QN - UF; ++i) {
+                qa[i] = qa[i + UF];
+                qb[i] = qb[i + UF];
+            }
+        }
 #pragma unroll
         for (int uu = 0; uu < UF; ++uu) {
             const int si = k0 + uu;            // 0-based stream index
             if (si >= S) break;
-            const int u = kUnroll ? uu : QL - 1;   // slot of the plane fed now
+            const int u = kUnroll ? uu : QL - 1 + uu;   // slot of the plane fed now
             ok = ok && mbar_wait_bounded(&full[slot], fph);
             if (!ok) break;
             const float *P = sm + slot * SLOT;
-            if (!kUnroll) {
-#pragma unroll
-                for (int i = 0; i < QL - 1; ++i) {
-                    qa[i] = qa[i + 1];
-                    qb[i] = qb[i + 1];
-                }
-            }
             ld4x2(P + C::AEL + 2 * C::TEL + cT, qa[u], qb[u]);   // plane zb + si - M
             if (si >= 2 * M) {
                 const int z = zb + si - 2 * M;
-                // queue slot of plane z + d is (u - M + d) mod QL
+                // queue slot of plane z + d: (u - M + d) mod QL unrolled, uu + M + d blocked
                 float win[4 + 2 * HX];
 #pragma unroll
                 for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
@@ -236,8 +248,9 @@ step3d_cross(const __grid_constant__ StepParams p)
                     f32x2 a01, a23, b01, b23;
                     ld4x2(P + cA + m * PW, a01, a23);
                     ld4x2(P + cA - m * PW, b01, b23);
-                    const int ip = (u - M + m + 2 * QL) % QL, im = (u - M - m + 2 * QL) % QL;
-                    const f32x2 wm = pk2(p.w[m], p.w[m]);
+                    const int ip = kUnroll ? (u - M + m + 2 * QL) % QL : uu + M + m;
+                    const int im = kUnroll ? (u - M - m + 2 * QL) % QL : uu + M - m;
+                    const f32x2 wm = p.w2[m];
                     const f32x2 x01 = pk2(win[HX + m] + win[HX - m], win[HX + 1 + m] + win[HX + 1 - m]);
                     const f32x2 x23 = pk2(win[HX + 2 + m] + win[HX + 2 - m], win[HX + 3 + m] + win[HX + 3 - m]);
                     const f32x2 s01 = add2(x01, add2(add2(a01, b01), add2(qa[ip], qa[im])));
@@ -251,7 +264,7 @@ step3d_cross(const __grid_constant__ StepParams p)
                 // the slot has been read: release it to the producer
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
-                const int ic = (u - M + 2 * QL) % QL;
+                const int ic = kUnroll ? (u - M + 2 * QL) % QL : uu + M;
                 const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
                 float g[4];
 #pragma unroll
@@ -264,14 +277,23 @@ step3d_cross(const __grid_constant__ StepParams p)
                 upk2(o23, o.z, o.w);
                 upk2(k01, kk.x, kk.y);
                 upk2(k23, kk.z, kk.w);
-                if (z >= zinj) zinj = inject_plane<MODE>(p, ki, kie, z, tx, ty, o, kk);
+                if (z >= zinj) {
+                    const InjOut r = inject_plane<MODE>(p, ki, kie, z, tx, ty, o, kk);
+                    o = r.o;
+                    ki = r.k;
+                    zinj = r.z;
+                }
                 if (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f || g[3] != 0.f) {
                     o.x = g[0] != 0.f ? __fdividef(o.x, 1.f + g[0]) : o.x;
                     o.y = g[1] != 0.f ? __fdividef(o.y, 1.f + g[1]) : o.y;
                     o.z = g[2] != 0.f ? __fdividef(o.z, 1.f + g[2]) : o.z;
                     o.w = g[3] != 0.f ? __fdividef(o.w, 1.f + g[3]) : o.w;
                 }
-                if (z >= zsmp) zsmp = sample_plane<MODE>(p, ks, kse, z, tx, ty, o, kk);
+                if (z >= zsmp) {
+                    const int2 r = sample_plane<MODE>(p, ks, kse, z, tx, ty, o, kk);
+                    ks = r.x;
+                    zsmp = r.y;
+                }
                 if (colok) {
                     const int64_t off = (int64_t)z * p.plane + colo;
                     *reinterpret_cast<float4 *>(p.u_prev + off) = o;
@@ -405,176 +427,185 @@ step3d_planar(const __grid_constant__ StepParams p)
     int zsmp = ks < kse ? p.smp[ks].z : 0x7fffffff;
     // acc[i] holds output P - M + i after the shift at plane P (i = 0..2M); the
     // accumulators move down one slot per plane (no unroll: small code)
-    float4 acc[QL];
+    // acc[uu + i][h] holds lanes (2h, 2h+1) of output P - M + i at sub-step uu
+    // of a block of UF planes (i = 0..2M); at the start of each block the
+    // accumulators move down UF slots and the top UF slots (outputs that start
+    // in this block) are cleared
+    constexpr int UF = 2;
+    constexpr int AN = QL + UF - 1;
+    f32x2 acc[AN][2];
 #pragma unroll
-    for (int i = 0; i < QL; ++i) acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < AN; ++i) acc[i][0] = acc[i][1] = 0ull;
     // centre values of the previous plane; the first plane's step only feeds
     // outputs below the chunk, so its start value does not matter
-    f32x2 cprev01 = 0ull, cprev23 = 0ull;
+    f32x2 cprev[2] = {0ull, 0ull};
     int slot = 0;
     uint32_t fph = 0;
     bool ok = true;
 
-    for (int t = 0; t < S; ++t) {
-        ok = ok && mbar_wait_bounded(&full[slot], fph);
+    for (int t0 = 0; t0 < S; t0 += UF) {
+#pragma unroll
+        for (int i = 0; i < AN; ++i) {
+            acc[i][0] = i + UF < AN ? acc[i + UF][0] : 0ull;
+            acc[i][1] = i + UF < AN ? acc[i + UF][1] : 0ull;
+        }
+#pragma unroll
+        for (int uu = 0; uu < UF; ++uu) {
+            const int t = t0 + uu;
+            if (t >= S) break;
+            ok = ok && mbar_wait_bounded(&full[slot], fph);
+            if (!ok) break;
+            const float *A = sm + slot * SLOT;
+            // Centre-free Laplacian, split per plane: T[s] sums the points of plane
+            // P at |dz| = s minus plane P's own centre value c(P) (n points, n c(P)
+            // subtracted before weighting); the z-axis remainder
+            // sum_s A_s (c(z+s) + c(z-s) - 2 c(z)), A_s the total weight at |dz| = s,
+            // is telescoped into plane-to-plane steps dl(P) = c(P) - c(P-1):
+            // output P - s gets +B_s dl(P) (s >= 1) and output P + s gets
+            // -B_{s+1} dl(P) (s >= 0), B_i = sum_{s >= i} A_s.  A constant field
+            // gives exactly zero, and every accumulated term is a small difference.
+            // Lanes (0,1) and (2,3) of the thread's float4 go two per instruction.
+            f32x2 T[M + 1][2];
+#pragma unroll
+            for (int s = 0; s <= M; ++s) T[s][0] = T[s][1] = 0ull;
+            f32x2 u2[2], u4[2], dl[2];
+            {   // row y of P: in-plane x line (s = 0) and xz lines (s >= 1)
+                float win[4 + 2 * HX];
+#pragma unroll
+                for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
+                    const float4 a = ld4(A + cA - HX + 4 * i);
+                    win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int b = HX + 2 * h;
+                    const f32x2 c = pk2(win[b], win[b + 1]);
+                    dl[h] = sub2(c, cprev[h]);
+                    cprev[h] = c;
+                    u2[h] = add2(c, c);
+                    u4[h] = add2(u2[h], u2[h]);
+                    f32x2 ps[M + 1];
+#pragma unroll
+                    for (int pp = 1; pp <= M; ++pp)
+                        ps[pp] = sub2(add2(pk2(win[b + pp], win[b + pp + 1]),
+                                           pk2(win[b - pp], win[b - pp + 1])), u2[h]);
+#pragma unroll
+                    for (int s = 0; s <= M; ++s) {
+                        const int E = shape_ext(SHAPE, M, 0, s);
+                        if (E < 1) continue;
+                        f32x2 a = mul2(p.w2[kW3 + s], ps[1]);
+#pragma unroll
+                        for (int pp = 2; pp <= E; ++pp)
+                            a = fma2(p.w2[pp * kW3 + s], ps[pp], a);
+                        T[s][h] = a;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 1; q <= M; ++q) {   // row pairs y +- q: in-plane rows and yz columns
+                const int E = shape_ext(SHAPE, M, 0, q);
+                const int E4 = round4(E);
+                float win[4 + 2 * HX];
+                const float *rp = A + cA + q * PW - E4;
+                const float *rm = A + cA - q * PW - E4;
+#pragma unroll
+                for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
+                    f32x2 a0, a1, b0, b1;
+                    ld4x2(rp + 4 * i, a0, a1);
+                    ld4x2(rm + 4 * i, b0, b1);
+                    upk2(add2(a0, b0), win[4 * i], win[4 * i + 1]);
+                    upk2(add2(a1, b1), win[4 * i + 2], win[4 * i + 3]);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int b = E4 + 2 * h;
+                    const f32x2 d0 = sub2(pk2(win[b], win[b + 1]), u2[h]);
+                    f32x2 a = mul2(p.w2[q], d0);
+#pragma unroll
+                    for (int pp = 1; pp <= E; ++pp)
+                        a = fma2(p.w2[pp * kW3 + q],
+                                 sub2(add2(pk2(win[b + pp], win[b + pp + 1]),
+                                           pk2(win[b - pp], win[b - pp + 1])), u4[h]), a);
+                    T[0][h] = add2(T[0][h], a);
+#pragma unroll
+                    for (int s = 1; s <= M; ++s)
+                        if (q <= shape_ext(SHAPE, M, 0, s))
+                            T[s][h] = fma2(p.w2[q * kW3 + s], d0, T[s][h]);
+                }
+            }
+            float4 cv = make_float4(0.f, 0.f, 0.f, 0.f), upv = cv, kpv = cv;
+            const bool fin = t >= 2 * M;
+            if (fin) {
+                cv = ld4(A + C::AEL + cT);
+                upv = ld4(A + C::AEL + C::TEL + cT);
+                kpv = ld4(A + C::AEL + 2 * C::TEL + cT);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if (++slot == NR) {
+                slot = 0;
+                fph ^= 1u;
+            }
+            // scatter: T[0] - B_1 dl -> output P (slot M); T[s] + B_s dl -> output
+            // P - s; T[s] - B_{s+1} dl -> output P + s
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                acc[uu + M][h] = add2(acc[uu + M][h], fma2(p.zm2[0], dl[h], T[0][h]));
+#pragma unroll
+                for (int s = 1; s <= M; ++s) {
+                    acc[uu + M - s][h] = add2(acc[uu + M - s][h],
+                                              fma2(p.zp2[s], dl[h], T[s][h]));
+                    const f32x2 tp = s < M ? fma2(p.zm2[s], dl[h], T[s][h])
+                                           : T[s][h];
+                    acc[uu + M + s][h] = add2(acc[uu + M + s][h], tp);
+                }
+            }
+            if (!fin) continue;
+            const int z = zb + t - 2 * M;             // output z = P - M is complete (slot 0)
+            const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
+            float g[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) g[j] = p.gcoef * (d2xy[j] + d2z);
+            f32x2 o01, o23;
+            const f32x2 dv01 = step_update2(pk2(cv.x, cv.y), pk2(upv.x, upv.y), pk2(kpv.x, kpv.y),
+                                            acc[uu][0], pk2(g[0], g[1]), o01);
+            const f32x2 dv23 = step_update2(pk2(cv.z, cv.w), pk2(upv.z, upv.w), pk2(kpv.z, kpv.w),
+                                            acc[uu][1], pk2(g[2], g[3]), o23);
+            float4 o;
+            upk2(o01, o.x, o.y);
+            upk2(o23, o.z, o.w);
+            if (z >= zinj) {
+                const InjOut r = inject_plane<MODE>(p, ki, kie, z, tx, ty, o, kpv);
+                o = r.o;
+                ki = r.k;
+                zinj = r.z;
+            }
+            if (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f || g[3] != 0.f) {
+                o.x = g[0] != 0.f ? __fdividef(o.x, 1.f + g[0]) : o.x;
+                o.y = g[1] != 0.f ? __fdividef(o.y, 1.f + g[1]) : o.y;
+                o.z = g[2] != 0.f ? __fdividef(o.z, 1.f + g[2]) : o.z;
+                o.w = g[3] != 0.f ? __fdividef(o.w, 1.f + g[3]) : o.w;
+            }
+            if (z >= zsmp) {
+                const int2 r = sample_plane<MODE>(p, ks, kse, z, tx, ty, o, kpv);
+                ks = r.x;
+                zsmp = r.y;
+            }
+            if (colok) {
+                const int64_t off = (int64_t)z * p.plane + colo;
+                *reinterpret_cast<float4 *>(p.u_prev + off) = o;
+                if (MODE != kModeAdjoint && p.dseg_out)
+                    *reinterpret_cast<ulonglong2 *>(p.dseg_out + off) = make_ulonglong2(dv01, dv23);
+                if (MODE == kModeAdjoint) {
+                    const float4 dd = ldg4(p.dseg_in + off);
+                    float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
+                    ga.x = fmaf(o.x, dd.x, ga.x); ga.y = fmaf(o.y, dd.y, ga.y);
+                    ga.z = fmaf(o.z, dd.z, ga.z); ga.w = fmaf(o.w, dd.w, ga.w);
+                    *reinterpret_cast<float4 *>(p.gacc + off) = ga;
+                }
+            }
+        }
         if (!ok) break;
-        const float *A = sm + slot * SLOT;
-#pragma unroll
-        for (int i = 0; i < QL - 1; ++i) acc[i] = acc[i + 1];
-        acc[QL - 1] = make_float4(0.f, 0.f, 0.f, 0.f);       // output P + M starts here
-        // Centre-free Laplacian, split per plane: T[s] sums the points of plane
-        // P at |dz| = s minus plane P's own centre value c(P) (n points, n c(P)
-        // subtracted before weighting); the z-axis remainder
-        // sum_s A_s (c(z+s) + c(z-s) - 2 c(z)), A_s the total weight at |dz| = s,
-        // is telescoped into plane-to-plane steps dl(P) = c(P) - c(P-1):
-        // output P - s gets +B_s dl(P) (s >= 1) and output P + s gets
-        // -B_{s+1} dl(P) (s >= 0), B_i = sum_{s >= i} A_s.  A constant field
-        // gives exactly zero, and every accumulated term is a small difference.
-        float T[M + 1][4];
-#pragma unroll
-        for (int s = 0; s <= M; ++s)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) T[s][j] = 0.f;
-        float u2[4], u4[4];
-        f32x2 dl01, dl23;
-        {   // row y of P: in-plane x line (s = 0) and xz lines (s >= 1)
-            float win[4 + 2 * HX];
-#pragma unroll
-            for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
-                const float4 a = ld4(A + cA - HX + 4 * i);
-                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
-            }
-            const f32x2 c01 = pk2(win[HX], win[HX + 1]), c23 = pk2(win[HX + 2], win[HX + 3]);
-            dl01 = sub2(c01, cprev01);
-            dl23 = sub2(c23, cprev23);
-            cprev01 = c01;
-            cprev23 = c23;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                u2[j] = win[HX + j] + win[HX + j];
-                u4[j] = u2[j] + u2[j];
-                float ps[M + 1];
-#pragma unroll
-                for (int pp = 1; pp <= M; ++pp) ps[pp] = (win[HX + j + pp] + win[HX + j - pp]) - u2[j];
-#pragma unroll
-                for (int s = 0; s <= M; ++s) {
-                    const int E = shape_ext(SHAPE, M, 0, s);
-                    if (E < 1) continue;
-                    float a = p.w[kWDim + s] * ps[1];
-#pragma unroll
-                    for (int pp = 2; pp <= E; ++pp) a = fmaf(p.w[pp * kWDim + s], ps[pp], a);
-                    T[s][j] = a;
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 1; q <= M; ++q) {   // row pairs y +- q: in-plane rows and yz columns
-            const int E = shape_ext(SHAPE, M, 0, q);
-            const int E4 = round4(E);
-            float win[4 + 2 * HX];
-            const float *rp = A + cA + q * PW - E4;
-            const float *rm = A + cA - q * PW - E4;
-#pragma unroll
-            for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
-                float4 a = ld4(rp + 4 * i);
-                const float4 b = ld4(rm + 4 * i);
-                a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float d0 = win[E4 + j] - u2[j];
-                float a = p.w[q] * d0;
-#pragma unroll
-                for (int pp = 1; pp <= E; ++pp)
-                    a = fmaf(p.w[pp * kWDim + q], (win[E4 + j + pp] + win[E4 + j - pp]) - u4[j], a);
-                T[0][j] += a;
-#pragma unroll
-                for (int s = 1; s <= M; ++s)
-                    if (q <= shape_ext(SHAPE, M, 0, s)) T[s][j] = fmaf(p.w[q * kWDim + s], d0, T[s][j]);
-            }
-        }
-        float4 cv = make_float4(0.f, 0.f, 0.f, 0.f), upv = cv, kpv = cv;
-        const bool fin = t >= 2 * M;
-        if (fin) {
-            cv = ld4(A + C::AEL + cT);
-            upv = ld4(A + C::AEL + C::TEL + cT);
-            kpv = ld4(A + C::AEL + 2 * C::TEL + cT);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[slot]);
-        if (++slot == NR) {
-            slot = 0;
-            fph ^= 1u;
-        }
-        // scatter: T[0] - B_1 dl -> output P (slot M); T[s] + B_s dl -> output
-        // P - s; T[s] - B_{s+1} dl -> output P + s
-        {
-            f32x2 a01, a23;
-            const f32x2 nb1 = pk2(-p.zarm[1], -p.zarm[1]);
-            f32x2 t01 = fma2(nb1, dl01, pk2(T[0][0], T[0][1]));
-            f32x2 t23 = fma2(nb1, dl23, pk2(T[0][2], T[0][3]));
-            a01 = add2(pk2(acc[M].x, acc[M].y), t01);
-            a23 = add2(pk2(acc[M].z, acc[M].w), t23);
-            upk2(a01, acc[M].x, acc[M].y);
-            upk2(a23, acc[M].z, acc[M].w);
-#pragma unroll
-            for (int s = 1; s <= M; ++s) {
-                const f32x2 ts01 = pk2(T[s][0], T[s][1]), ts23 = pk2(T[s][2], T[s][3]);
-                const f32x2 bm = pk2(p.zarm[s], p.zarm[s]);
-                float4 &am = acc[M - s];
-                t01 = fma2(bm, dl01, ts01);
-                t23 = fma2(bm, dl23, ts23);
-                a01 = add2(pk2(am.x, am.y), t01); upk2(a01, am.x, am.y);
-                a23 = add2(pk2(am.z, am.w), t23); upk2(a23, am.z, am.w);
-                float4 &ap = acc[M + s];
-                if (s < M) {
-                    const f32x2 bp = pk2(-p.zarm[s + 1], -p.zarm[s + 1]);
-                    t01 = fma2(bp, dl01, ts01);
-                    t23 = fma2(bp, dl23, ts23);
-                } else {
-                    t01 = ts01;
-                    t23 = ts23;
-                }
-                a01 = add2(pk2(ap.x, ap.y), t01); upk2(a01, ap.x, ap.y);
-                a23 = add2(pk2(ap.z, ap.w), t23); upk2(a23, ap.z, ap.w);
-            }
-        }
-        if (!fin) continue;
-        const int z = zb + t - 2 * M;             // output z = P - M is complete (slot 0)
-        const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
-        float g[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) g[j] = p.gcoef * (d2xy[j] + d2z);
-        f32x2 o01, o23;
-        const f32x2 dv01 = step_update2(pk2(cv.x, cv.y), pk2(upv.x, upv.y), pk2(kpv.x, kpv.y),
-                                        pk2(acc[0].x, acc[0].y), pk2(g[0], g[1]), o01);
-        const f32x2 dv23 = step_update2(pk2(cv.z, cv.w), pk2(upv.z, upv.w), pk2(kpv.z, kpv.w),
-                                        pk2(acc[0].z, acc[0].w), pk2(g[2], g[3]), o23);
-        float4 o;
-        upk2(o01, o.x, o.y);
-        upk2(o23, o.z, o.w);
-        if (z >= zinj) zinj = inject_plane<MODE>(p, ki, kie, z, tx, ty, o, kpv);
-        if (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f || g[3] != 0.f) {
-            o.x = g[0] != 0.f ? __fdividef(o.x, 1.f + g[0]) : o.x;
-            o.y = g[1] != 0.f ? __fdividef(o.y, 1.f + g[1]) : o.y;
-            o.z = g[2] != 0.f ? __fdividef(o.z, 1.f + g[2]) : o.z;
-            o.w = g[3] != 0.f ? __fdividef(o.w, 1.f + g[3]) : o.w;
-        }
-        if (z >= zsmp) zsmp = sample_plane<MODE>(p, ks, kse, z, tx, ty, o, kpv);
-        if (colok) {
-            const int64_t off = (int64_t)z * p.plane + colo;
-            *reinterpret_cast<float4 *>(p.u_prev + off) = o;
-            if (MODE != kModeAdjoint && p.dseg_out)
-                *reinterpret_cast<ulonglong2 *>(p.dseg_out + off) = make_ulonglong2(dv01, dv23);
-            if (MODE == kModeAdjoint) {
-                const float4 dd = ldg4(p.dseg_in + off);
-                float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
-                ga.x = fmaf(o.x, dd.x, ga.x); ga.y = fmaf(o.y, dd.y, ga.y);
-                ga.z = fmaf(o.z, dd.z, ga.z); ga.w = fmaf(o.w, dd.w, ga.w);
-                *reinterpret_cast<float4 *>(p.gacc + off) = ga;
-            }
-        }
     }
     if (!ok) {
         atomicOr(p.status, kStatusTimeout);
