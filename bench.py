@@ -57,6 +57,28 @@ def dist_env():
     return rank, world, local
 
 
+# DRAM bytes per padded point of one step launch (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the 300^3 case, 360^3 padded;
+# scaled to the bench grid by its point count), valid only for the kernel
+# sources whose digest is recorded with them.
+TRAFFIC_SOURCES = ("paper_2606_04882_gb300/csrc/step3d.cu",
+                   "paper_2606_04882_gb300/csrc/device_common.cuh",
+                   "paper_2606_04882_gb300/csrc/internal.h")
+TRAFFIC_DIGEST = "5af76fe0bdccf7a79dce09b139b19a540368e35fb2fdc3c373c9e61c00ae8cf0"
+TRAFFIC_B_PER_POINT = {"cross8_spatte": 16.659, "rhombus4_displs": 17.079}
+
+
+def traffic_per_launch(stencil, pts):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != TRAFFIC_DIGEST or stencil not in TRAFFIC_B_PER_POINT:
+        return None
+    return TRAFFIC_B_PER_POINT[stencil] * pts
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -242,7 +264,9 @@ def run_gpu(args):
                         "gpts": pts / (launch_ms * 1e-3) / 1e9})
     dom = max(range(len(runs)), key=lambda i: per_run_ms[i])
     roof = {"bound": "hbm", "achieved": kernels[dom]["achieved_gbs"], "peak": peak,
-            "unit": "GB/s", "frac": kernels[dom]["frac"], "traffic": None,
+            "unit": "GB/s", "frac": kernels[dom]["frac"],
+            "traffic": traffic_per_launch(kernels[dom]["stencil"], pts),
+            "traffic_note": "DRAM bytes per launch, ncu on 360^3 scaled by points",
             "kernel": "step3d " + kernels[dom]["stencil"],
             "bytes_per_point": 16, "peak_source": peak_kind}
 
