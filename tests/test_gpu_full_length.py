@@ -1,0 +1,73 @@
+"""Full-length parity of the 3D workloads against the FP64 oracle.
+
+The 400^3 forward (460^3 padded, 1500 steps) and the 256^3 FWI gradient
+(296^3 padded, 1200 steps) are compared with oracle runs of the same length
+on the same inputs: relative L2 <= 1e-4 on traces, final wavefields and the
+gradient.  The oracle needs 5 to 20 minutes of all host cores per case, so
+these tests run only with FDWAVE_FULL_LENGTH=1; the default GPU suite checks
+the same workloads at full size through restarts and reduced step counts."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as WL
+from gpu_cases import Case, rel_l2
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("FDWAVE_FULL_LENGTH") != "1",
+                                 reason="set FDWAVE_FULL_LENGTH=1 (long oracle runs)")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_04882_gb300 import build
+    build.build()
+
+
+def _case(pr, st):
+    import paper_2606_04882_gb300 as F
+    dt = 0.5 * F.fd_cfl_limit(F.stencil_desc(pr.dim, "cross", st.M)) * pr.h / pr.vmax
+    return Case(pr.vel, pr.h, pr.nt, pr.nb, pr.vmax, st.shape, st.M, st.N, st.scheme,
+                src=pr.src, rec=pr.rec, f0=pr.f0, dt=dt)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_gradient_random_400_full_run(k):
+    pr = WL.gradient_random_3d()
+    c = _case(pr, pr.stencils[k])
+    tr, sf, rc = c.gpu_forward()
+    assert rc == 0
+    otr, ost = c.oracle_forward()
+    e_tr, e_u = rel_l2(tr, otr), rel_l2(sf[0], ost[0])
+    print("full-length %s%d: traces %.3g, final field %.3g" % (c.shape, c.M, e_tr, e_u))
+    assert e_tr < 1e-4 and e_u < 1e-4
+
+
+def test_fwi_256_full_gradient():
+    import torch
+    import paper_2606_04882_gb300 as F
+    from oracle import physics as P
+    from oracle import wave as W
+    probs, _ = WL.fwi_3d()
+    pr = probs[0]
+    c = _case(pr, WL.Stencil("cross", 4, 0, "spatte"))
+    resid = np.random.default_rng(7).standard_normal((c.nt, len(c.rec)))
+    plan = c.plan()
+    dev = torch.device("cuda")
+    g = torch.empty(c.vel.shape, device=dev)
+    ws = F.workspace(plan.gradient_workspace_size(1, len(c.rec), 20))
+    F.fd_adjoint_gradient(plan, torch.from_numpy(c.vel).to(dev), plan.linear_index(c.src),
+                          torch.from_numpy(c.wavelet32()).to(dev), plan.linear_index(c.rec),
+                          torch.from_numpy(resid.astype(np.float32)).to(dev), 20, g, ws)
+    assert F.fd_status_read(plan, ws) == 0
+    gg = g.cpu().numpy()
+    del ws
+    og, _ = W.gradient(c.setup(), c.nt, c.src, P.ricker(c.f0, c.nt, c.dt)[:, None], c.rec,
+                       resid)
+    e = rel_l2(gg, og)
+    print("full-length FWI gradient: %.3g" % e)
+    assert e < 1e-4
