@@ -153,6 +153,7 @@ def run_gpu(args):
         desc = F.stencil_desc(3, shape, M, 0, scheme, courant=vmax * dt / h)
         plan = F.Plan(pr.shape, h, dt, nt, nb, vmax, desc)
         plan0 = F.Plan(pr.shape, h, dt, 0, nb, vmax, desc)      # set-up only (nt = 0)
+        tile = list(plan.autotune(vel).tile)                     # untimed tile-shape choice
         if src_idx is None:
             src_idx = plan.linear_index(pr.src)
             rec_idx = plan.linear_index(pr.rec)
@@ -160,7 +161,7 @@ def run_gpu(args):
         tr = torch.empty((nt, len(rec_idx)), device=dev)
         ws = F.workspace(plan.forward_workspace_size(1, len(rec_idx)), dev)
         runs.append(dict(name="%s%d_%s" % (shape, M, scheme), plan=plan, plan0=plan0, wav=wav,
-                         tr=tr, ws=ws, dt=dt))
+                         tr=tr, ws=ws, dt=dt, tile=tile))
     inf = runs[0]["plan"].info()
     pts = int(inf.padded[0] * inf.padded[1] * inf.padded[2])
     stream = torch.cuda.current_stream()
@@ -259,7 +260,7 @@ def run_gpu(args):
     for i, r in enumerate(runs):
         launch_ms = max(per_run_ms[i] - setup_ms[i], 1e-9) / nt
         gbs = 16.0 * pts / (launch_ms * 1e-3) / 1e9
-        kernels.append({"stencil": r["name"], "ms_per_launch": launch_ms,
+        kernels.append({"stencil": r["name"], "tile": r["tile"], "ms_per_launch": launch_ms,
                         "achieved_gbs": gbs, "frac": gbs / peak,
                         "gpts": pts / (launch_ms * 1e-3) / 1e9})
     dom = max(range(len(runs)), key=lambda i: per_run_ms[i])
