@@ -81,9 +81,9 @@ struct StepParams {
 };
 
 // Batched 2D shots: per-shot descriptor in device memory (128-byte aligned, as
-// CUtensorMap is) and the launch parameters of one time step.
-struct alignas(128) ShotDesc {
-    CUtensorMap tmap[2];       // halo-box maps of field buffers 0 and 1
+// CUtensorMap is) and the launch parameters of one time step.  ShotInfo is the
+// scalar part, which the batched kernel stages into shared memory per tile.
+struct ShotInfo {
     float *buf[2];             // buffer 0 holds u^0 at the start, buffer 1 u^{-1}
     const float *kappa;
     const int32_t *inj_ptr;
@@ -98,10 +98,18 @@ struct alignas(128) ShotDesc {
     int tiles_x, inj_ncol, smp_ncol;
 };
 
+struct alignas(128) ShotDesc {
+    CUtensorMap tmap[2];       // halo-box maps of field buffers 0 and 1
+    CUtensorMap tile[2];       // tile maps (no halo) of field buffers 0 and 1
+    CUtensorMap ktile;         // tile map of kappa
+    ShotInfo info;
+};
+
 struct BatchParams {
     const ShotDesc *shots;
     const int32_t *tile_shot;  // global tile -> shot
     const int32_t *tile_local; // global tile -> tile within the shot
+    int ntiles;                // tiles of all shots
     int step;                  // time step n (field parity and series row)
     int *status;
     float w[kWDim * kWDim];

@@ -303,7 +303,8 @@ int encode_field_map(const fd_plan *p, CUtensorMap *map, const float *base, bool
     if (p->prob.dim == 2) {
         dims[0] = p->pad[2]; dims[1] = p->pad[0];
         str[0] = p->pitch * 4;
-        box[0] = p->var.box[0]; box[1] = p->var.box[1];
+        box[0] = tile ? p->var.tbox[0] : p->var.box[0];
+        box[1] = tile ? p->var.tbox[1] : p->var.box[1];
         return encode_tmap(map, base, 2, dims, str, box);
     }
     dims[0] = p->pad[2]; dims[1] = p->pad[1]; dims[2] = p->pad[0];
@@ -1075,28 +1076,32 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
             std::memset(&d, 0, sizeof d);
             Variant keep = p->var;
             p->var = bv;     // maps with the batch's box
-            int r0 = encode_field_map(p, &d.tmap[0], As[i], false);
-            int r1 = encode_field_map(p, &d.tmap[1], Bs[i], false);
+            const float *kap = reinterpret_cast<const float *>(base + L.kappa);
+            int r = encode_field_map(p, &d.tmap[0], As[i], false);
+            r = r ? r : encode_field_map(p, &d.tmap[1], Bs[i], false);
+            r = r ? r : encode_field_map(p, &d.tile[0], As[i], true);
+            r = r ? r : encode_field_map(p, &d.tile[1], Bs[i], true);
+            r = r ? r : encode_field_map(p, &d.ktile, kap, true);
             p->var = keep;
-            if (r0 || r1) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-            d.buf[0] = As[i];
-            d.buf[1] = Bs[i];
-            d.kappa = reinterpret_cast<const float *>(base + L.kappa);
-            d.inj_ptr = sh.nsrc ? ip : nullptr;
-            d.inj = ie;
-            d.inj_series = sh.wavelet_d;
-            d.inj_ncol = sh.nsrc;
-            d.smp_ptr = sh.nrec ? sp_ : nullptr;
-            d.smp = se;
-            d.smp_out = sh.traces_d;
-            d.smp_ncol = sh.nrec;
-            d.nx = p->pad[2];
-            d.nz = p->pad[0];
-            d.pitch = p->pitch;
-            d.phys_lo[0] = p->prob.nb; d.phys_hi[0] = p->prob.nb + p->prob.n[2] - 1;
-            d.phys_lo[2] = p->prob.nb; d.phys_hi[2] = p->prob.nb + p->prob.n[0] - 1;
-            d.gcoef = p->gcoef;
-            d.tiles_x = geo[i].tiles_x;
+            if (r) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+            d.info.buf[0] = As[i];
+            d.info.buf[1] = Bs[i];
+            d.info.kappa = reinterpret_cast<const float *>(base + L.kappa);
+            d.info.inj_ptr = sh.nsrc ? ip : nullptr;
+            d.info.inj = ie;
+            d.info.inj_series = sh.wavelet_d;
+            d.info.inj_ncol = sh.nsrc;
+            d.info.smp_ptr = sh.nrec ? sp_ : nullptr;
+            d.info.smp = se;
+            d.info.smp_out = sh.traces_d;
+            d.info.smp_ncol = sh.nrec;
+            d.info.nx = p->pad[2];
+            d.info.nz = p->pad[0];
+            d.info.pitch = p->pitch;
+            d.info.phys_lo[0] = p->prob.nb; d.info.phys_hi[0] = p->prob.nb + p->prob.n[2] - 1;
+            d.info.phys_lo[2] = p->prob.nb; d.info.phys_hi[2] = p->prob.nb + p->prob.n[0] - 1;
+            d.info.gcoef = p->gcoef;
+            d.info.tiles_x = geo[i].tiles_x;
             for (int t = 0; t < geo[i].ntiles; ++t) {
                 tshot.push_back(i);
                 tlocal.push_back(t);
@@ -1130,6 +1135,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         bp.shots = reinterpret_cast<const ShotDesc *>(d);
         bp.tile_shot = reinterpret_cast<const int32_t *>(t1);
         bp.tile_local = reinterpret_cast<const int32_t *>(t2);
+        bp.ntiles = ntiles;
         // shot 0's status word collects the device conditions of the batch
         bp.status = reinterpret_cast<int *>(ws);
         std::memcpy(bp.w, p0->W, sizeof bp.w);

@@ -8,6 +8,8 @@
 // by one TMA load whose out-of-bounds elements are zero-filled: that is the
 // zero field outside the padded grid.  Thread (tx, ty) owns 4 consecutive
 // columns (one float4) of R consecutive rows.
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace fdw {
@@ -29,6 +31,80 @@ __device__ __forceinline__ void for_owned(const int32_t *ptr, const PtEntry *tab
         const int zl = en.z - z0 - ty * R;
         const int xl = en.yx & 0xffff;
         if (zl >= 0 && zl < R && (xl >> 2) == tx) f(zl, xl & 3, en);
+    }
+}
+
+// Laplacian sum of the 4 columns owned by thread column tx in shared-memory
+// row zl (the tile plus halo, row width kTX + 2 round4(M)); cc receives the
+// centre values.
+template <int SHAPE, int M, int NN, class PP>
+__device__ __forceinline__ void lap2d_row(const PP &p, const float *sm, int zl, int tx,
+                                          float (&cc)[4], float (&lap)[4])
+{
+    constexpr int HX = round4(M);
+    constexpr int SW = kTX + 2 * HX;
+    const float4 c = ld4(sm + zl * SW + HX + 4 * tx);
+    cc[0] = c.x; cc[1] = c.y; cc[2] = c.z; cc[3] = c.w;
+    float u2[4], u4[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        u2[j] = cc[j] + cc[j];
+        u4[j] = u2[j] + u2[j];
+    }
+    // Centre-free Laplacian: sum_o a_o (u(x+o) - u(x)), the same sum since
+    // the weights of a consistent stencil add up to zero.  Each group of n
+    // points has n u(x) subtracted before it is weighted, so a constant
+    // field gives exactly zero whatever the FP32 rounding of the weights,
+    // and the accumulator only holds small differences.
+    lap[0] = lap[1] = lap[2] = lap[3] = 0.f;
+    if (SHAPE == FD_CROSS) {
+        // x and z arms of offset m share the weight W[0][m]
+        float win[4 + 2 * HX];
+#pragma unroll
+        for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
+            const float4 a = ld4(sm + zl * SW + 4 * tx + 4 * i);
+            win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+        }
+#pragma unroll
+        for (int m = 1; m <= M; ++m) {
+            const float4 a = ld4(sm + (zl + m) * SW + HX + 4 * tx);
+            const float4 b = ld4(sm + (zl - m) * SW + HX + 4 * tx);
+            const float zp[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                lap[j] = fmaf(p.w[m], ((win[HX + j + m] + win[HX + j - m]) + zp[j]) - u4[j],
+                              lap[j]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q <= M; ++q) {
+            const int E = shape_ext(SHAPE, M, NN, q);
+            if (E < 0) continue;
+            const int E4 = round4(E);
+            float win[4 + 2 * round4(M)];
+            const float *rp = sm + (zl + q) * SW + HX + 4 * tx - E4;
+            const float *rm = sm + (zl - q) * SW + HX + 4 * tx - E4;
+#pragma unroll
+            for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
+                float4 a = ld4(rp + 4 * i);
+                if (q > 0) {
+                    const float4 b = ld4(rm + 4 * i);
+                    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+                }
+                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                // row pair z +- q holds 2 points at dx = 0 and 4 at dx = +-pp;
+                // row z holds the centre (no term) and 2 points at +-pp
+                const float un = q > 0 ? u4[j] : u2[j];
+                float acc = q > 0 ? p.w[q] * (win[E4 + j] - u2[j]) : 0.f;   // W[0][q]
+#pragma unroll
+                for (int pp = 1; pp <= E; ++pp)
+                    acc = fmaf(p.w[pp * kWDim + q], (win[E4 + j + pp] + win[E4 + j - pp]) - un, acc);
+                lap[j] += acc;
+            }
+        }
     }
 }
 
@@ -88,69 +164,8 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
     for (int r = 0; r < R; ++r) {
         const int zl = M + ty * R + r;
         const int zg = z0 + ty * R + r;
-        const float4 c = ld4(sm + zl * SW + HX + 4 * tx);
-        const float cc[4] = {c.x, c.y, c.z, c.w};
-        float u2[4], u4[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            u2[j] = cc[j] + cc[j];
-            u4[j] = u2[j] + u2[j];
-        }
-        // Centre-free Laplacian: sum_o a_o (u(x+o) - u(x)), the same sum since
-        // the weights of a consistent stencil add up to zero.  Each group of n
-        // points has n u(x) subtracted before it is weighted, so a constant
-        // field gives exactly zero whatever the FP32 rounding of the weights,
-        // and the accumulator only holds small differences.
-        float lap[4] = {0.f, 0.f, 0.f, 0.f};
-        if (SHAPE == FD_CROSS) {
-            // x and z arms of offset m share the weight W[0][m]
-            float win[4 + 2 * HX];
-#pragma unroll
-            for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
-                const float4 a = ld4(sm + zl * SW + 4 * tx + 4 * i);
-                win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
-            }
-#pragma unroll
-            for (int m = 1; m <= M; ++m) {
-                const float4 a = ld4(sm + (zl + m) * SW + HX + 4 * tx);
-                const float4 b = ld4(sm + (zl - m) * SW + HX + 4 * tx);
-                const float zp[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    lap[j] = fmaf(p.w[m], ((win[HX + j + m] + win[HX + j - m]) + zp[j]) - u4[j],
-                                  lap[j]);
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q <= M; ++q) {
-                const int E = shape_ext(SHAPE, M, NN, q);
-                if (E < 0) continue;
-                const int E4 = round4(E);
-                float win[4 + 2 * round4(M)];
-                const float *rp = sm + (zl + q) * SW + HX + 4 * tx - E4;
-                const float *rm = sm + (zl - q) * SW + HX + 4 * tx - E4;
-#pragma unroll
-                for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
-                    float4 a = ld4(rp + 4 * i);
-                    if (q > 0) {
-                        const float4 b = ld4(rm + 4 * i);
-                        a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-                    }
-                    win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    // row pair z +- q holds 2 points at dx = 0 and 4 at dx = +-pp;
-                    // row z holds the centre (no term) and 2 points at +-pp
-                    const float un = q > 0 ? u4[j] : u2[j];
-                    float acc = q > 0 ? p.w[q] * (win[E4 + j] - u2[j]) : 0.f;   // W[0][q]
-#pragma unroll
-                    for (int pp = 1; pp <= E; ++pp)
-                        acc = fmaf(p.w[pp * kWDim + q], (win[E4 + j + pp] + win[E4 + j - pp]) - un, acc);
-                    lap[j] += acc;
-                }
-            }
-        }
+        float cc[4], lap[4];
+        lap2d_row<SHAPE, M, NN>(p, sm, zl, tx, cc, lap);
         const float d2z = layer_d2(zg, p.phys_lo[2], p.phys_hi[2]);
         const float uu[4] = {up[r].x, up[r].y, up[r].z, up[r].w};
         const float kk[4] = {kp[r].x, kp[r].y, kp[r].z, kp[r].w};
@@ -207,39 +222,32 @@ __global__ void __launch_bounds__(kThreads) step2d_kernel(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// Batched shots: one launch per time step over the tiles of every shot.  A
-// CTA finds its shot and local tile in two tables and reads the shot's
-// descriptor (tensor maps of both field buffers, pointers, sizes, point
-// tables) from device memory; the weights stay in kernel parameters.
+// Batched shots: one launch per time step over the tiles of every shot.  The
+// CTAs are persistent and walk the tile table with a stride of gridDim.x.  A
+// producer warp stages each tile in one of NB shared-memory slots: by TMA the
+// halo box of u^n and the u^{n-1} and kappa tiles, and by plain copies the
+// shot's scalars and the tile's ranges in the point tables; each slot has a
+// full and an empty mbarrier, so the copies of the next tiles overlap the
+// arithmetic of the current one.  The weights stay in kernel parameters.
 // ---------------------------------------------------------------------------
 struct BatchView {
-    const CUtensorMap *tmap;
     float *u_prev;
-    const float *kappa;
     int64_t nx, nz, pitch;
     int64_t phys_lo[3], phys_hi[3];
     float gcoef;
     int tiles_x;
-    const int32_t *inj_ptr;
     const PtEntry *inj;
     const float *inj_series;
     int inj_ncol;
-    const int32_t *smp_ptr;
     const PtEntry *smp;
     float *smp_out;
     int smp_ncol;
     int step;
-    float *dseg_out;
-    const float *dseg_in;
-    float *gacc;
-    int *status;
     const float (&w)[kWDim * kWDim];
-    __device__ BatchView(const ShotDesc &d, const BatchParams &bp)
-        : tmap(&d.tmap[bp.step & 1]), u_prev(d.buf[(bp.step & 1) ^ 1]), kappa(d.kappa), nx(d.nx),
-          nz(d.nz), pitch(d.pitch), gcoef(d.gcoef), tiles_x(d.tiles_x), inj_ptr(d.inj_ptr),
-          inj(d.inj), inj_series(d.inj_series), inj_ncol(d.inj_ncol), smp_ptr(d.smp_ptr),
-          smp(d.smp), smp_out(d.smp_out), smp_ncol(d.smp_ncol), step(bp.step), dseg_out(nullptr),
-          dseg_in(nullptr), gacc(nullptr), status(bp.status), w(bp.w)
+    __device__ BatchView(const ShotInfo &d, const BatchParams &bp)
+        : u_prev(d.buf[(bp.step & 1) ^ 1]), nx(d.nx), nz(d.nz), pitch(d.pitch), gcoef(d.gcoef),
+          tiles_x(d.tiles_x), inj(d.inj), inj_series(d.inj_series), inj_ncol(d.inj_ncol),
+          smp(d.smp), smp_out(d.smp_out), smp_ncol(d.smp_ncol), step(bp.step), w(bp.w)
     {
         for (int i = 0; i < 3; ++i) {
             phys_lo[i] = d.phys_lo[i];
@@ -248,14 +256,186 @@ struct BatchView {
     }
 };
 
-template <int SHAPE, int M, int R>
-__global__ void __launch_bounds__(kThreads) step2d_batched(const __grid_constant__ BatchParams bp)
+// What the producer warp stages for a slot besides the field data: the
+// shot's scalars, the tile and its ranges in the injection and sampling tables.
+struct Staged {
+    ShotInfo info;
+    int tile, ib, ie, sb, se;
+};
+
+// Apply f(j, entry) to the entries [b, e) of a point table that lie in row zg
+// and in thread column tx.
+template <class F>
+__device__ __forceinline__ void for_row(const PtEntry *tab, int b, int e, int zg, int tx, F f)
 {
+    for (int k = b; k < e; ++k) {
+        const PtEntry en = tab[k];
+        const int xl = en.yx & 0xffff;
+        if (en.z == zg && (xl >> 2) == tx) f(xl & 3, en);
+    }
+}
+
+template <int M, int R>
+struct StreamCfg {
+    static constexpr int HX = round4(M);
+    static constexpr int SW = kTX + 2 * HX;
+    static constexpr int SH = kTZ * R + 2 * M;
+    static constexpr int AEL = (SW * SH + 31) & ~31;   // halo box, 128-byte padded
+    static constexpr int TEL = kTX * kTZ * R;          // one tile
+    static constexpr int SLOT = AEL + 2 * TEL;         // halo box | u_prev tile | kappa tile
+    // as many slots (2 to 4) as fit in about 110 KB, so that two CTAs share an
+    // SM and each keeps up to NB - 1 tiles of copies in flight
+    static constexpr int NB = 110 * 1024 / (SLOT * 4) < 2 ? 2
+                            : 110 * 1024 / (SLOT * 4) > 4 ? 4 : 110 * 1024 / (SLOT * 4);
+    static constexpr size_t SMEM = (size_t)NB * SLOT * sizeof(float);
+    static constexpr int NCW = kThreads / 32;          // consumer warps
+    static constexpr int THREADS = kThreads + 32;
+};
+
+// Forward step of one staged tile.
+template <int SHAPE, int M, int R>
+__device__ __forceinline__ void stream_tile(const BatchView &v, const Staged &st,
+                                            const float *slot, int tx, int ty)
+{
+    using C = StreamCfg<M, R>;
+    const int tile = st.tile;
+    const int x0 = (tile % v.tiles_x) * kTX;
+    const int z0 = (tile / v.tiles_x) * (kTZ * R);
+    const int xg = x0 + 4 * tx;
+    const bool colok = xg < v.nx;
+    float d2x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d2x[j] = layer_d2(xg + j, v.phys_lo[0], v.phys_hi[0]);
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const int rr = ty * R + r;
+        const int zg = z0 + rr;
+        float cc[4], lap[4];
+        lap2d_row<SHAPE, M, 0>(v, slot, M + rr, tx, cc, lap);
+        const float4 up = ld4(slot + C::AEL + rr * kTX + 4 * tx);
+        const float4 kp = ld4(slot + C::AEL + C::TEL + rr * kTX + 4 * tx);
+        const float uu[4] = {up.x, up.y, up.z, up.w};
+        const float kk[4] = {kp.x, kp.y, kp.z, kp.w};
+        const float d2z = layer_d2(zg, v.phys_lo[2], v.phys_hi[2]);
+        float o[4], g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            g[j] = v.gcoef * (d2x[j] + d2z);
+            step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
+        }
+        if (st.ib < st.ie)
+            for_row(v.inj, st.ib, st.ie, zg, tx, [&](int j, const PtEntry &en) {
+                const float a = en.scale * v.inj_series[(int64_t)v.step * v.inj_ncol + en.col];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj == j) o[jj] += a;
+            });
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+        if (st.sb < st.se)
+            for_row(v.smp, st.sb, st.se, zg, tx, [&](int j, const PtEntry &en) {
+                float s = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj == j) s = o[jj];
+                v.smp_out[(int64_t)v.step * v.smp_ncol + en.col] = s * en.scale;
+            });
+        if (!colok || zg >= v.nz) continue;
+        *reinterpret_cast<float4 *>(v.u_prev + (int64_t)zg * v.pitch + xg) =
+            make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+template <int SHAPE, int M, int R>
+__global__ void __launch_bounds__(StreamCfg<M, R>::THREADS)
+step2d_batched(const __grid_constant__ BatchParams bp)
+{
+    using C = StreamCfg<M, R>;
+    constexpr int NB = C::NB;
+    constexpr uint32_t BYTES = (C::SW * C::SH + 2 * C::TEL) * 4;
     extern __shared__ __align__(1024) float sm[];
-    __shared__ uint64_t bar;
-    const int g = blockIdx.x;
-    const BatchView v(bp.shots[bp.tile_shot[g]], bp);
-    step2d_tile<SHAPE, M, 0, kModeForward, R>(v, bp.tile_local[g], sm, bar);
+    __shared__ uint64_t full[NB], empty[NB];
+    __shared__ Staged staged[NB];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < NB; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], C::NCW);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int G = gridDim.x;
+    const int cur = bp.step & 1;
+
+    if (warp == C::NCW) {   // producer: lane 0 waits and issues, the warp copies
+        volatile int *abort_v = &abort_flag;
+        constexpr int kWords = sizeof(ShotInfo) / 4;
+        int i = 0;
+        for (int g = blockIdx.x; g < bp.ntiles; g += G, ++i) {
+            const int b = i % NB;
+            int go = 1;
+            if (lane == 0) {
+                if (i >= NB && !mbar_wait_bounded(&empty[b], (uint32_t)((i / NB - 1) & 1))) {
+                    atomicOr(bp.status, kStatusTimeout);
+                    *abort_v = 1;
+                }
+                go = !*abort_v;
+            }
+            if (!__shfl_sync(0xffffffffu, go, 0)) break;
+            const int shot = bp.tile_shot[g], tile = bp.tile_local[g];
+            const ShotDesc &d = bp.shots[shot];
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(&d.info);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&staged[b].info);
+            for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
+            if (lane == 0) {
+                const ShotInfo &in = d.info;
+                staged[b].tile = tile;
+                staged[b].ib = in.inj_ptr ? in.inj_ptr[tile] : 0;
+                staged[b].ie = in.inj_ptr ? in.inj_ptr[tile + 1] : 0;
+                staged[b].sb = in.smp_ptr ? in.smp_ptr[tile] : 0;
+                staged[b].se = in.smp_ptr ? in.smp_ptr[tile + 1] : 0;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                // the staged words above are released to the consumers by the arrive
+                __threadfence_block();
+                const int ntx = d.info.tiles_x;
+                const int x0 = (tile % ntx) * kTX, z0 = (tile / ntx) * (kTZ * R);
+                float *fd = sm + b * C::SLOT;
+                mbar_arrive_expect_tx(&full[b], BYTES);
+                tma_load_2d(fd, &d.tmap[cur], &full[b], x0 - C::HX, z0 - M);
+                tma_load_2d(fd + C::AEL, &d.tile[cur ^ 1], &full[b], x0, z0);
+                tma_load_2d(fd + C::AEL + C::TEL, &d.ktile, &full[b], x0, z0);
+            }
+        }
+        if (lane == 0 && *abort_v) {   // let the copies in flight land before the block exits
+            for (int j = i > NB ? i - NB : 0; j < i; ++j)
+                mbar_wait_bounded(&full[j % NB], (j / NB) & 1, 100000000LL);
+        }
+        return;
+    }
+
+    const int tx = tid & 15, ty = tid >> 4;
+    bool ok = true;
+    int i = 0;
+    for (int g = blockIdx.x; g < bp.ntiles; g += G, ++i) {
+        const int b = i % NB;
+        if (*reinterpret_cast<volatile int *>(&abort_flag)) break;
+        ok = mbar_wait_bounded(&full[b], (i / NB) & 1);
+        if (!ok) break;
+        const BatchView v(staged[b].info, bp);
+        stream_tile<SHAPE, M, R>(v, staged[b], sm + b * C::SLOT, tx, ty);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+    }
+    if (!ok) {
+        atomicOr(bp.status, kStatusTimeout);
+        *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -484,8 +664,7 @@ BatchFn lookup_batched(int shape, int M, int R)
 {
 #define FDW_B(S, MM, RR) \
     if (shape == S && M == MM && R == RR) return step2d_batched<S, MM, RR>;
-    FDW_B(FD_CROSS, 2, 1) FDW_B(FD_CROSS, 4, 1) FDW_B(FD_CROSS, 8, 1)
-    FDW_B(FD_CROSS, 2, 4) FDW_B(FD_CROSS, 4, 4) FDW_B(FD_CROSS, 8, 4)
+    FDW_B(FD_CROSS, 2, 2) FDW_B(FD_CROSS, 4, 2) FDW_B(FD_CROSS, 8, 2)
 #undef FDW_B
     return nullptr;
 }
@@ -534,20 +713,25 @@ cudaError_t launch_persist2d(const Variant &v, const PersistParams &pp, int grid
 
 int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v)
 {
-    const int R = total_tiles4 >= 2 * 152 ? 4 : 1;
+    // 64 x 32 tiles (R = 2): small slots, so each CTA keeps several tiles of
+    // copies in flight while it computes one
+    const int R = 2;
+    (void)total_tiles4;
     if (!lookup_batched(shape, M, R)) return FD_ERR_UNSUPPORTED;
     v->dim = 2;
     v->shape = shape;
     v->M = M;
     v->N = 0;
     v->generic = 0;
-    v->threads = kThreads;
+    v->threads = kThreads + 32;
     v->tx = kTX;
     v->tz = kTZ * R;
     v->box[0] = kTX + 2 * round4(M);
     v->box[1] = kTZ * R + 2 * M;
     v->box[2] = 1;
-    v->smem = (size_t)v->box[0] * v->box[1] * sizeof(float);
+    v->tbox[0] = kTX;
+    v->tbox[1] = kTZ * R;
+    v->smem = M == 2 ? StreamCfg<2, 2>::SMEM : M == 4 ? StreamCfg<4, 2>::SMEM : StreamCfg<8, 2>::SMEM;
     return FD_OK;
 }
 
@@ -558,7 +742,14 @@ cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
     if (e != cudaSuccess) return e;
     if (ntiles <= 0) return cudaSuccess;
-    fn<<<ntiles, kThreads, v.smem, s>>>(bp);
+    // persistent CTAs: as many as are resident at once, at most one per tile
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, v.threads, v.smem)) != cudaSuccess)
+        return e;
+    const int grid = std::min(ntiles, std::max(1, per_sm) * sms);
+    fn<<<grid, v.threads, v.smem, s>>>(bp);
     return cudaGetLastError();
 }
 
