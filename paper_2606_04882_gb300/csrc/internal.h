@@ -105,10 +105,15 @@ struct alignas(128) ShotDesc {
     ShotInfo info;
 };
 
+// One tile of a batch: its shot, its index and origin in the shot's grid, and
+// its ranges in the shot's injection and sampling tables.
+struct alignas(16) TileRec {
+    int shot, tile, x0, z0, ib, ie, sb, se;
+};
+
 struct BatchParams {
     const ShotDesc *shots;
-    const int32_t *tile_shot;  // global tile -> shot
-    const int32_t *tile_local; // global tile -> tile within the shot
+    const TileRec *tiles;      // every shot's tiles, shot by shot
     int ntiles;                // tiles of all shots
     int step;                  // time step n (field parity and series row)
     int *status;

@@ -993,7 +993,7 @@ bool batch_geometry(int nshots, const fd_shot *shots, Variant &bv, std::vector<T
 
 size_t batch_extra_bytes(int nshots, int64_t ntiles)
 {
-    return up(nshots * sizeof(ShotDesc)) + 2 * up(ntiles * sizeof(int32_t));
+    return up(nshots * sizeof(ShotDesc)) + up(ntiles * sizeof(TileRec));
 }
 
 }  // namespace
@@ -1044,7 +1044,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
     char *base = reinterpret_cast<char *>(ws);
     std::vector<StepParams> sps(one ? 0 : nshots);
     std::vector<ShotDesc> descs(one ? nshots : 0);
-    std::vector<int32_t> tshot, tlocal;
+    std::vector<TileRec> recs;
     std::vector<float *> As(nshots), Bs(nshots);
     std::vector<const CUtensorMap *> mp(nshots);
     for (int i = 0; i < nshots; ++i) {
@@ -1102,9 +1102,19 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
             d.info.phys_lo[2] = p->prob.nb; d.info.phys_hi[2] = p->prob.nb + p->prob.n[0] - 1;
             d.info.gcoef = p->gcoef;
             d.info.tiles_x = geo[i].tiles_x;
+            const int32_t *hip = reinterpret_cast<const int32_t *>(T.blob.data() + T.inj_ptr);
+            const int32_t *hsp = reinterpret_cast<const int32_t *>(T.blob.data() + T.smp_ptr);
             for (int t = 0; t < geo[i].ntiles; ++t) {
-                tshot.push_back(i);
-                tlocal.push_back(t);
+                TileRec r;
+                r.shot = i;
+                r.tile = t;
+                r.x0 = (t % geo[i].tiles_x) * geo[i].tx;
+                r.z0 = (t / geo[i].tiles_x) * geo[i].tz;
+                r.ib = sh.nsrc ? hip[t] : 0;
+                r.ie = sh.nsrc ? hip[t + 1] : 0;
+                r.sb = sh.nrec ? hsp[t] : 0;
+                r.se = sh.nrec ? hsp[t + 1] : 0;
+                recs.push_back(r);
             }
         } else {
             if ((st = upload_maps(p, L, base, 2, s))) return st;
@@ -1124,17 +1134,14 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
     }
     BatchParams bp;
     std::memset(&bp, 0, sizeof bp);
-    const int ntiles = (int)tshot.size();
+    const int ntiles = (int)recs.size();
     if (one) {
         char *d = base;
         FDW_CK(cudaMemcpyAsync(d, descs.data(), nshots * sizeof(ShotDesc), cudaMemcpyHostToDevice, s));
         char *t1 = d + up(nshots * sizeof(ShotDesc));
-        char *t2 = t1 + up(ntiles * sizeof(int32_t));
-        FDW_CK(cudaMemcpyAsync(t1, tshot.data(), ntiles * 4, cudaMemcpyHostToDevice, s));
-        FDW_CK(cudaMemcpyAsync(t2, tlocal.data(), ntiles * 4, cudaMemcpyHostToDevice, s));
+        FDW_CK(cudaMemcpyAsync(t1, recs.data(), ntiles * sizeof(TileRec), cudaMemcpyHostToDevice, s));
         bp.shots = reinterpret_cast<const ShotDesc *>(d);
-        bp.tile_shot = reinterpret_cast<const int32_t *>(t1);
-        bp.tile_local = reinterpret_cast<const int32_t *>(t2);
+        bp.tiles = reinterpret_cast<const TileRec *>(t1);
         bp.ntiles = ntiles;
         // shot 0's status word collects the device conditions of the batch
         bp.status = reinterpret_cast<int *>(ws);

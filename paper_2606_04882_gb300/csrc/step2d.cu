@@ -260,7 +260,7 @@ struct BatchView {
 // shot's scalars, the tile and its ranges in the injection and sampling tables.
 struct Staged {
     ShotInfo info;
-    int tile, ib, ie, sb, se;
+    TileRec rec;
 };
 
 // Apply f(j, entry) to the entries [b, e) of a point table that lie in row zg
@@ -298,9 +298,7 @@ __device__ __forceinline__ void stream_tile(const BatchView &v, const Staged &st
                                             const float *slot, int tx, int ty)
 {
     using C = StreamCfg<M, R>;
-    const int tile = st.tile;
-    const int x0 = (tile % v.tiles_x) * kTX;
-    const int z0 = (tile / v.tiles_x) * (kTZ * R);
+    const int x0 = st.rec.x0, z0 = st.rec.z0;
     const int xg = x0 + 4 * tx;
     const bool colok = xg < v.nx;
     float d2x[4];
@@ -323,8 +321,8 @@ __device__ __forceinline__ void stream_tile(const BatchView &v, const Staged &st
             g[j] = v.gcoef * (d2x[j] + d2z);
             step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
         }
-        if (st.ib < st.ie)
-            for_row(v.inj, st.ib, st.ie, zg, tx, [&](int j, const PtEntry &en) {
+        if (st.rec.ib < st.rec.ie)
+            for_row(v.inj, st.rec.ib, st.rec.ie, zg, tx, [&](int j, const PtEntry &en) {
                 const float a = en.scale * v.inj_series[(int64_t)v.step * v.inj_ncol + en.col];
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
@@ -333,8 +331,8 @@ __device__ __forceinline__ void stream_tile(const BatchView &v, const Staged &st
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
-        if (st.sb < st.se)
-            for_row(v.smp, st.sb, st.se, zg, tx, [&](int j, const PtEntry &en) {
+        if (st.rec.sb < st.rec.se)
+            for_row(v.smp, st.rec.sb, st.rec.se, zg, tx, [&](int j, const PtEntry &en) {
                 float s = 0.f;
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
@@ -375,8 +373,11 @@ step2d_batched(const __grid_constant__ BatchParams bp)
         volatile int *abort_v = &abort_flag;
         constexpr int kWords = sizeof(ShotInfo) / 4;
         int i = 0;
+        TileRec next = blockIdx.x < bp.ntiles ? bp.tiles[blockIdx.x] : TileRec{};
         for (int g = blockIdx.x; g < bp.ntiles; g += G, ++i) {
             const int b = i % NB;
+            const TileRec rec = next;
+            if (g + G < bp.ntiles) next = bp.tiles[g + G];     // one record ahead
             int go = 1;
             if (lane == 0) {
                 if (i >= NB && !mbar_wait_bounded(&empty[b], (uint32_t)((i / NB - 1) & 1))) {
@@ -386,30 +387,23 @@ step2d_batched(const __grid_constant__ BatchParams bp)
                 go = !*abort_v;
             }
             if (!__shfl_sync(0xffffffffu, go, 0)) break;
-            const int shot = bp.tile_shot[g], tile = bp.tile_local[g];
-            const ShotDesc &d = bp.shots[shot];
+            const ShotDesc &d = bp.shots[rec.shot];
+            if (lane == 0) {   // field data first; the arrival below closes the phase
+                float *fd = sm + b * C::SLOT;
+                mbar_expect_tx(&full[b], BYTES);
+                tma_load_2d(fd, &d.tmap[cur], &full[b], rec.x0 - C::HX, rec.z0 - M);
+                tma_load_2d(fd + C::AEL, &d.tile[cur ^ 1], &full[b], rec.x0, rec.z0);
+                tma_load_2d(fd + C::AEL + C::TEL, &d.ktile, &full[b], rec.x0, rec.z0);
+                staged[b].rec = rec;
+            }
             const uint32_t *src = reinterpret_cast<const uint32_t *>(&d.info);
             uint32_t *dst = reinterpret_cast<uint32_t *>(&staged[b].info);
             for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
-            if (lane == 0) {
-                const ShotInfo &in = d.info;
-                staged[b].tile = tile;
-                staged[b].ib = in.inj_ptr ? in.inj_ptr[tile] : 0;
-                staged[b].ie = in.inj_ptr ? in.inj_ptr[tile + 1] : 0;
-                staged[b].sb = in.smp_ptr ? in.smp_ptr[tile] : 0;
-                staged[b].se = in.smp_ptr ? in.smp_ptr[tile + 1] : 0;
-            }
             __syncwarp();
             if (lane == 0) {
                 // the staged words above are released to the consumers by the arrive
                 __threadfence_block();
-                const int ntx = d.info.tiles_x;
-                const int x0 = (tile % ntx) * kTX, z0 = (tile / ntx) * (kTZ * R);
-                float *fd = sm + b * C::SLOT;
-                mbar_arrive_expect_tx(&full[b], BYTES);
-                tma_load_2d(fd, &d.tmap[cur], &full[b], x0 - C::HX, z0 - M);
-                tma_load_2d(fd + C::AEL, &d.tile[cur ^ 1], &full[b], x0, z0);
-                tma_load_2d(fd + C::AEL + C::TEL, &d.ktile, &full[b], x0, z0);
+                mbar_arrive(&full[b]);
             }
         }
         if (lane == 0 && *abort_v) {   // let the copies in flight land before the block exits
