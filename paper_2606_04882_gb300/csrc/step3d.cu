@@ -18,6 +18,16 @@ namespace {
 
 constexpr int kTX3 = 64;
 
+// Ring depth of the warp-specialised pipelines: as many plane slots (4 to 8)
+// as fit the shared memory of one CTA when 2 (TY = 16) or 3 (TY = 8) CTAs
+// share an SM; deeper rings keep more planes of copies in flight.
+__host__ __device__ constexpr int ring_depth(int slot_floats, int ty)
+{
+    const int budget = ty >= 16 ? 110 * 1024 : 72 * 1024;
+    const int n = budget / (slot_floats * 4);
+    return n < 4 ? 4 : n > 8 ? 8 : n;
+}
+
 // Tile table walk for one plane: apply f(j, entry) to owned entries with
 // entry.z == z; `k` advances past them (entries are z-sorted per tile).
 template <class F>
@@ -96,7 +106,7 @@ struct CrossCfg {
     static constexpr int AEL = (PW * PH + 31) & ~31;      // halo plane (floats, padded)
     static constexpr int TEL = kTX3 * TY;                 // tile (floats, multiple of 32)
     static constexpr int SLOT = AEL + 3 * TEL;            // A | u_prev | kappa | queue tile
-    static constexpr int NR = 4;                          // ring depth
+    static constexpr int NR = ring_depth(SLOT, TY);
     static constexpr int NCW = TY / 2;                    // consumer warps
     static constexpr int THREADS = 16 * TY + 32;
 };
@@ -332,7 +342,7 @@ struct PlanarCfg {
     static constexpr int AEL = (PW * PH + 31) & ~31;
     static constexpr int TEL = kTX3 * TY;
     static constexpr int SLOT = AEL + 3 * TEL;            // A | u_cur(P-M) | u_prev | kappa
-    static constexpr int NR = 4;
+    static constexpr int NR = ring_depth(SLOT, TY);
     static constexpr int NCW = TY / 2;
     static constexpr int THREADS = 16 * TY + 32;
 };
@@ -673,7 +683,7 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
     {   // warp-specialised pipelines (cross and planar): one extra producer warp
         const int HXc = round4(M);
         const int A = ((kTX3 + 2 * HXc) * (ty + 2 * M) + 31) & ~31;
-        v->smem = (size_t)4 * (A + 3 * kTX3 * ty) * sizeof(float);
+        v->smem = (size_t)ring_depth(A + 3 * kTX3 * ty, ty) * (A + 3 * kTX3 * ty) * sizeof(float);
         v->threads = 16 * ty + 32;
     }
     (void)nx; (void)ny; (void)nz;
