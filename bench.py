@@ -312,6 +312,7 @@ def run_other(args):
             desc = F.stencil_desc(2, st.shape, st.M, 0, st.scheme, courant=pr.vmax * pw_dt / pr.h)
             plan = F.Plan(pr.shape, pr.h, pw_dt, pr.nt, pr.nb, pr.vmax, desc)
             plan0 = F.Plan(pr.shape, pr.h, pw_dt, 0, pr.nb, pr.vmax, desc)
+            plan.autotune(vel)                                       # untimed tile choice
             si, ri = plan.linear_index(pr.src), plan.linear_index(pr.rec)
             wav = torch.from_numpy(F.fd_ricker(pr.f0, pw_dt, pr.nt)[:, None].copy()).to(dev)
             tr = torch.empty((pr.nt, len(ri)), device=dev)
@@ -363,6 +364,7 @@ def run_other(args):
         dt = 0.5 * F.fd_cfl_limit(F.stencil_desc(3, "cross", 4)) * pr0.h / pr0.vmax
         plan = F.Plan(pr0.shape, pr0.h, dt, pr0.nt, pr0.nb, pr0.vmax, F.stencil_desc(3, "cross", 4))
         m = torch.from_numpy((1.0 / pr0.vel.astype(np.float64) ** 2).astype(np.float32)).to(dev)
+        plan.autotune(m, F.FD_MODEL_SLOWNESS2)                       # untimed tile choice
         ri = plan.linear_index(pr0.rec)
         wav = torch.from_numpy(F.fd_ricker(pr0.f0, dt, pr0.nt)[:, None].copy()).to(dev)
         resid = torch.randn((pr0.nt, len(ri)), device=dev, generator=torch.Generator(dev).manual_seed(5))
