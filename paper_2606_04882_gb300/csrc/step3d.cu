@@ -23,7 +23,7 @@ constexpr int kTX3 = 64;
 // share an SM; deeper rings keep more planes of copies in flight.
 __host__ __device__ constexpr int ring_depth(int slot_floats, int ty)
 {
-    const int budget = ty >= 16 ? 110 * 1024 : 72 * 1024;
+    const int budget = ty >= 16 ? 80 * 1024 : 72 * 1024;
     const int n = budget / (slot_floats * 4);
     return n < 4 ? 4 : n > 8 ? 8 : n;
 }
