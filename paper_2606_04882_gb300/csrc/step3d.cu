@@ -18,12 +18,20 @@ namespace {
 
 constexpr int kTX3 = 64;
 
-// Ring depth of the warp-specialised pipelines: as many plane slots (4 to 8)
-// as fit the shared memory of one CTA when 2 (TY = 16) or 3 (TY = 8) CTAs
-// share an SM; deeper rings keep more planes of copies in flight.
-__host__ __device__ constexpr int ring_depth(int slot_floats, int ty)
+// CTAs per SM the warp-specialised pipelines are built for: 2 with 64 x 16
+// tiles; with 64 x 8 tiles 4 for the cross up to M = 4 (96 registers per
+// thread suffice) and 3 otherwise (the planar kernels run faster with the
+// registers of 3).
+__host__ __device__ constexpr int ctas_per_sm(bool cross, int M, int ty)
 {
-    const int budget = ty >= 16 ? 80 * 1024 : 72 * 1024;
+    return ty >= 16 ? 2 : (cross && M <= 4 ? 4 : 3);
+}
+
+// Ring depth: as many plane slots (4 to 8) as fit the shared memory of one
+// CTA at that residency; deeper rings keep more planes of copies in flight.
+__host__ __device__ constexpr int ring_depth(int slot_floats, int ctas)
+{
+    const int budget = (ctas <= 2 ? 80 : ctas == 3 ? 72 : 54) * 1024;
     const int n = budget / (slot_floats * 4);
     return n < 4 ? 4 : n > 8 ? 8 : n;
 }
@@ -106,13 +114,14 @@ struct CrossCfg {
     static constexpr int AEL = (PW * PH + 31) & ~31;      // halo plane (floats, padded)
     static constexpr int TEL = kTX3 * TY;                 // tile (floats, multiple of 32)
     static constexpr int SLOT = AEL + 3 * TEL;            // A | u_prev | kappa | queue tile
-    static constexpr int NR = ring_depth(SLOT, TY);
+    static constexpr int MINB = ctas_per_sm(true, M, TY);
+    static constexpr int NR = ring_depth(SLOT, MINB);
     static constexpr int NCW = TY / 2;                    // consumer warps
     static constexpr int THREADS = 16 * TY + 32;
 };
 
 template <int M, int MODE, int TY>
-__global__ void __launch_bounds__(CrossCfg<M, TY>::THREADS, TY == 16 ? 2 : 3)
+__global__ void __launch_bounds__(CrossCfg<M, TY>::THREADS, CrossCfg<M, TY>::MINB)
 step3d_cross(const __grid_constant__ StepParams p)
 {
     using C = CrossCfg<M, TY>;
@@ -342,13 +351,14 @@ struct PlanarCfg {
     static constexpr int AEL = (PW * PH + 31) & ~31;
     static constexpr int TEL = kTX3 * TY;
     static constexpr int SLOT = AEL + 3 * TEL;            // A | u_cur(P-M) | u_prev | kappa
-    static constexpr int NR = ring_depth(SLOT, TY);
+    static constexpr int MINB = ctas_per_sm(false, M, TY);
+    static constexpr int NR = ring_depth(SLOT, MINB);
     static constexpr int NCW = TY / 2;
     static constexpr int THREADS = 16 * TY + 32;
 };
 
 template <int SHAPE, int M, int MODE, int TY>
-__global__ void __launch_bounds__(PlanarCfg<M, TY>::THREADS, TY == 16 ? 2 : 3)
+__global__ void __launch_bounds__(PlanarCfg<M, TY>::THREADS, PlanarCfg<M, TY>::MINB)
 step3d_planar(const __grid_constant__ StepParams p)
 {
     using C = PlanarCfg<M, TY>;
@@ -683,7 +693,7 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
     {   // warp-specialised pipelines (cross and planar): one extra producer warp
         const int HXc = round4(M);
         const int A = ((kTX3 + 2 * HXc) * (ty + 2 * M) + 31) & ~31;
-        v->smem = (size_t)ring_depth(A + 3 * kTX3 * ty, ty) * (A + 3 * kTX3 * ty) * sizeof(float);
+        v->smem = (size_t)ring_depth(A + 3 * kTX3 * ty, ctas_per_sm(shape == FD_CROSS, M, ty)) * (A + 3 * kTX3 * ty) * sizeof(float);
         v->threads = 16 * ty + 32;
     }
     (void)nx; (void)ny; (void)nz;
