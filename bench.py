@@ -64,8 +64,8 @@ def dist_env():
 TRAFFIC_SOURCES = ("paper_2606_04882_gb300/csrc/step3d.cu",
                    "paper_2606_04882_gb300/csrc/device_common.cuh",
                    "paper_2606_04882_gb300/csrc/internal.h")
-TRAFFIC_DIGEST = "b536d9b3af9da59109afab72e058c5bca555cc98add8cee4fbac10b606daa8d7"
-TRAFFIC_B_PER_POINT = {"cross4_spatte": 16.491, "cross8_spatte": 16.459, "rhombus4_displs": 16.373}
+TRAFFIC_DIGEST = "e4e0d9ced09aded231e36e8205d7ac44302eaa934727a9355e9f8e7cae6abe96"
+TRAFFIC_B_PER_POINT = {"cross4_spatte": 16.975, "cross8_spatte": 16.733, "rhombus4_displs": 16.510}
 
 
 def traffic_per_launch(stencil, pts):
