@@ -216,3 +216,25 @@ def test_constant_field_is_a_fixed_point(dim, shape, M, N, scheme):
     assert rc == 0
     inner = (slice(None),) + tuple(slice(nb, nb + s) for s in n)
     assert np.array_equal(st[inner][0], st0[inner][0])
+
+
+@pytest.mark.parametrize("shape,M,scheme", [("cross", 4, "spatte"), ("cross", 8, "spatte"),
+                                            ("rhombus", 4, "displs"), ("square", 2, "displs")])
+def test_edge_cases_3d(shape, M, scheme):
+    """3D grids smaller than one tile and than the stencil radius, sources and
+    receivers on corners, no sponge, and a thin grid whose z extent is shorter
+    than the stencil, each against the oracle."""
+    # grid smaller than a tile and than the radius in every axis
+    vel = np.full((5, 6, 7), 2000.0, np.float32)
+    c = Case(vel, 10.0, 12, 0, 2000.0, shape, M, 0, scheme, src=[[0, 0, 0]],
+             rec=[[4, 5, 6], [0, 0, 0], [2, 3, 4]])
+    tr, st, rc = c.gpu_forward()
+    otr, ost = c.oracle_forward()
+    assert rc == 0 and rel_l2(tr, otr) < TOL and rel_l2(st[0], ost[0]) < TOL
+    # thin in z, wide in x and y (several tiles with ragged tails), with a sponge
+    vel = smooth_velocity((3, 37, 131), 9, 1500.0, 3000.0, sigma=3.0)
+    c = Case(vel, 10.0, 25, 2, 3000.0, shape, M, 0, scheme, src=[[1, 18, 65], [2, 36, 130]],
+             rec=[[0, y, x] for y in (0, 36) for x in range(0, 131, 13)])
+    tr, st, rc = c.gpu_forward()
+    otr, ost = c.oracle_forward()
+    assert rc == 0 and rel_l2(tr, otr) < TOL and rel_l2(st[0], ost[0]) < TOL
