@@ -34,16 +34,15 @@ __device__ __forceinline__ void for_owned(const int32_t *ptr, const PtEntry *tab
     }
 }
 
-// Laplacian sum of the 4 columns owned by thread column tx in shared-memory
-// row zl (the tile plus halo, row width kTX + 2 round4(M)); cc receives the
-// centre values.
-template <int SHAPE, int M, int NN, class PP>
-__device__ __forceinline__ void lap2d_row(const PP &p, const float *sm, int zl, int tx,
-                                          float (&cc)[4], float (&lap)[4])
+// Laplacian sum of 4 consecutive columns col0 .. col0+3 of shared-memory row zl
+// (row width SW floats, at least round4(M) columns of halo on either side of
+// them, col0 a multiple of 4); cc receives the centre values.
+template <int SHAPE, int M, int NN, int SW, class PP>
+__device__ __forceinline__ void lap2d_at(const PP &p, const float *sm, int zl, int col0,
+                                         float (&cc)[4], float (&lap)[4])
 {
     constexpr int HX = round4(M);
-    constexpr int SW = kTX + 2 * HX;
-    const float4 c = ld4(sm + zl * SW + HX + 4 * tx);
+    const float4 c = ld4(sm + zl * SW + col0);
     cc[0] = c.x; cc[1] = c.y; cc[2] = c.z; cc[3] = c.w;
     float u2[4], u4[4];
 #pragma unroll
@@ -62,13 +61,13 @@ __device__ __forceinline__ void lap2d_row(const PP &p, const float *sm, int zl, 
         float win[4 + 2 * HX];
 #pragma unroll
         for (int i = 0; i < (4 + 2 * HX) / 4; ++i) {
-            const float4 a = ld4(sm + zl * SW + 4 * tx + 4 * i);
+            const float4 a = ld4(sm + zl * SW + col0 - HX + 4 * i);
             win[4 * i] = a.x; win[4 * i + 1] = a.y; win[4 * i + 2] = a.z; win[4 * i + 3] = a.w;
         }
 #pragma unroll
         for (int m = 1; m <= M; ++m) {
-            const float4 a = ld4(sm + (zl + m) * SW + HX + 4 * tx);
-            const float4 b = ld4(sm + (zl - m) * SW + HX + 4 * tx);
+            const float4 a = ld4(sm + (zl + m) * SW + col0);
+            const float4 b = ld4(sm + (zl - m) * SW + col0);
             const float zp[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -82,8 +81,8 @@ __device__ __forceinline__ void lap2d_row(const PP &p, const float *sm, int zl, 
             if (E < 0) continue;
             const int E4 = round4(E);
             float win[4 + 2 * round4(M)];
-            const float *rp = sm + (zl + q) * SW + HX + 4 * tx - E4;
-            const float *rm = sm + (zl - q) * SW + HX + 4 * tx - E4;
+            const float *rp = sm + (zl + q) * SW + col0 - E4;
+            const float *rm = sm + (zl - q) * SW + col0 - E4;
 #pragma unroll
             for (int i = 0; i < (4 + 2 * E4) / 4; ++i) {
                 float4 a = ld4(rp + 4 * i);
@@ -106,6 +105,15 @@ __device__ __forceinline__ void lap2d_row(const PP &p, const float *sm, int zl, 
             }
         }
     }
+}
+
+// The same for thread column tx of a tile staged with its halo (row width
+// kTX + 2 round4(M)).
+template <int SHAPE, int M, int NN, class PP>
+__device__ __forceinline__ void lap2d_row(const PP &p, const float *sm, int zl, int tx,
+                                          float (&cc)[4], float (&lap)[4])
+{
+    lap2d_at<SHAPE, M, NN, kTX + 2 * round4(M)>(p, sm, zl, round4(M) + 4 * tx, cc, lap);
 }
 
 // One tile of the 2D step.  PP is the parameter view: StepParams for a
