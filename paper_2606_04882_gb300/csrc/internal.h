@@ -84,7 +84,8 @@ struct StepParams {
 // CUtensorMap is) and the launch parameters of one time step.  ShotInfo is the
 // scalar part, which the batched kernel stages into shared memory per tile.
 struct ShotInfo {
-    float *buf[2];             // buffer 0 holds u^0 at the start, buffer 1 u^{-1}
+    float *buf[4];             // buffer 0 holds u^0 at the start, buffer 1 u^{-1};
+                               // 2 and 3 are used by the two-step kernel
     const float *kappa;
     const int32_t *inj_ptr;
     const PtEntry *inj;
@@ -102,6 +103,11 @@ struct alignas(128) ShotDesc {
     CUtensorMap tmap[2];       // halo-box maps of field buffers 0 and 1
     CUtensorMap tile[2];       // tile maps (no halo) of field buffers 0 and 1
     CUtensorMap ktile;         // tile map of kappa
+    // two-step kernel: u^n box with a 2M-row halo and the u^{n-1} and kappa
+    // boxes with an M-row halo, per field buffer (0..3) and for kappa
+    CUtensorMap c2[4];
+    CUtensorMap p2[4];
+    CUtensorMap k2;
     ShotInfo info;
 };
 
@@ -109,11 +115,18 @@ struct alignas(128) ShotDesc {
 // its ranges in the shot's injection and sampling tables.
 struct alignas(16) TileRec {
     int shot, tile, x0, z0, ib, ie, sb, se;
+    int xb, xe;                // two-step kernel: range in BatchParams::ext
+    int pad[2];
 };
 
 struct BatchParams {
     const ShotDesc *shots;
     const TileRec *tiles;      // every shot's tiles, shot by shot
+    // two-step kernel: source entries of each tile's extended region (x
+    // relative to the region's origin), and the buffers holding u^n, u^{n-1}
+    // and receiving u^{n+1}, u^{n+2}
+    const PtEntry *ext;
+    int roles[4];
     int ntiles;                // tiles of all shots
     int step;                  // time step n (field parity and series row)
     int *status;
@@ -156,6 +169,14 @@ int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v);
 int persist2d_grid(const Variant &v, int ntiles);
 cudaError_t launch_persist2d(const Variant &v, const PersistParams &pp, int grid, cudaStream_t s);
 cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s);
+// Two-step batched kernel (u^{n+1} and u^{n+2} per pass): geometry of its
+// boxes for cross stencils with M <= 4 (FD_ERR_UNSUPPORTED otherwise).
+struct Batch2Geo {
+    int tz, hx, hxc;           // tile rows; x halo of the extended region; x halo of the u^n box
+    int cbox[2], pbox[2];      // u^n box and u^{n-1} / kappa box (x, z extents)
+};
+int batch2d2_geometry(int shape, int M, Batch2Geo *g);
+cudaError_t launch_batched2d2(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s);
 
 // aux kernels
 cudaError_t launch_prep_kappa(const float *model, int kind, float *kappa, int dim,

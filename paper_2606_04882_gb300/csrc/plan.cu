@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -995,9 +996,32 @@ bool batch_geometry(int nshots, const fd_shot *shots, Variant &bv, std::vector<T
     return true;
 }
 
-size_t batch_extra_bytes(int nshots, int64_t ntiles)
+// Extra workspace of a single-launch batch: descriptors, tile records and,
+// when the two-step kernel supports the stencil, two more field buffers per
+// shot and the extended-region source table (a source lies in at most four
+// tiles' extended regions).
+size_t batch_extra_bytes(int nshots, const fd_shot *shots, int64_t ntiles, bool two)
 {
-    return up(nshots * sizeof(ShotDesc)) + up(ntiles * sizeof(TileRec));
+    size_t b = up(nshots * sizeof(ShotDesc)) + up(ntiles * sizeof(TileRec));
+    if (two) {
+        int64_t nsrc = 0;
+        for (int i = 0; i < nshots; ++i) {
+            b += 2 * up(shots[i].plan->field * sizeof(float));
+            nsrc += shots[i].nsrc;
+        }
+        b += up(std::max<int64_t>(4 * nsrc, 1) * sizeof(PtEntry));
+    }
+    return b;
+}
+
+// The two-step kernel applies to single-launch batches of its stencils with at
+// least two steps (FDWAVE_BATCH_2STEP=0 turns it off).
+bool batch_two_step(const fd_plan *p0, bool one, Batch2Geo *g)
+{
+    if (!one || p0->prob.nt < 2 || batch2d2_geometry(p0->shape_eff, p0->st.M, g) != FD_OK)
+        return false;
+    const char *e = std::getenv("FDWAVE_BATCH_2STEP");
+    return !(e && std::strcmp(e, "0") == 0);
 }
 
 }  // namespace
@@ -1018,7 +1042,10 @@ extern "C" int fd_forward_batched_workspace_size(int nshots, const fd_shot *shot
         tot += make_layout(shots[i].plan, shots[i].nsrc, shots[i].nrec, false, 1, nt_tab).total;
         if (one) ntiles += geo[i].ntiles;
     }
-    if (one) tot += batch_extra_bytes(nshots, ntiles);
+    Batch2Geo g2;
+    const bool two = nshots > 0 && one && shots[0].plan->prob.nt >= 2 &&
+                     batch2d2_geometry(shots[0].plan->shape_eff, shots[0].plan->st.M, &g2) == FD_OK;
+    if (one) tot += batch_extra_bytes(nshots, shots, ntiles, two);
     *bytes = tot;
     return FD_OK;
 }
@@ -1044,8 +1071,27 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
     Variant bv;
     std::vector<TileGeo> geo;
     const bool one = batch_geometry(nshots, shots, bv, geo);
+    Batch2Geo g2;
+    const bool two_cap = one && p0->prob.nt >= 2 &&
+                         batch2d2_geometry(p0->shape_eff, p0->st.M, &g2) == FD_OK;
+    const bool two = two_cap && batch_two_step(p0, one, &g2);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = reinterpret_cast<char *>(ws);
+    // extra region (after every shot's slice): descriptors | tile records |
+    // two-step buffers of each shot | extended-region source table
+    int64_t ntiles_all = 0;
+    size_t shots_bytes = 0;
+    for (int i = 0; i < nshots; ++i) {
+        shots_bytes += make_layout(shots[i].plan, shots[i].nsrc, shots[i].nrec, false, 1,
+                                   one ? geo[i].ntiles : -1).total;
+        if (one) ntiles_all += geo[i].ntiles;
+    }
+    char *extra = base + shots_bytes;
+    char *xbufs = extra + up(nshots * sizeof(ShotDesc)) + up(ntiles_all * sizeof(TileRec));
+    char *xtab = xbufs;
+    if (two_cap)
+        for (int i = 0; i < nshots; ++i) xtab += 2 * up(shots[i].plan->field * sizeof(float));
+    std::vector<PtEntry> ext;
     std::vector<StepParams> sps(one ? 0 : nshots);
     std::vector<ShotDesc> descs(one ? nshots : 0);
     std::vector<TileRec> recs;
@@ -1088,6 +1134,24 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
             r = r ? r : encode_field_map(p, &d.ktile, kap, true);
             p->var = keep;
             if (r) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+            if (two_cap) {
+                float *f2 = reinterpret_cast<float *>(xbufs);
+                float *f3 = reinterpret_cast<float *>(xbufs + up(p->field * sizeof(float)));
+                xbufs += 2 * up(p->field * sizeof(float));
+                FDW_CK(cudaMemsetAsync(f2, 0, (size_t)p->field * 4, s));
+                FDW_CK(cudaMemsetAsync(f3, 0, (size_t)p->field * 4, s));
+                d.info.buf[2] = f2;
+                d.info.buf[3] = f3;
+                const float *bufs[4] = {As[i], Bs[i], f2, f3};
+                const int64_t dims[2] = {p->pad[2], p->pad[0]};
+                const int64_t str[1] = {p->pitch * 4};
+                for (int b = 0; b < 4 && !r; ++b) {
+                    r = encode_tmap(&d.c2[b], bufs[b], 2, dims, str, g2.cbox);
+                    r = r ? r : encode_tmap(&d.p2[b], bufs[b], 2, dims, str, g2.pbox);
+                }
+                r = r ? r : encode_tmap(&d.k2, kap, 2, dims, str, g2.pbox);
+                if (r) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+            }
             d.info.buf[0] = As[i];
             d.info.buf[1] = Bs[i];
             d.info.kappa = reinterpret_cast<const float *>(base + L.kappa);
@@ -1108,10 +1172,42 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
             d.info.tiles_x = geo[i].tiles_x;
             const int32_t *hip = reinterpret_cast<const int32_t *>(T.blob.data() + T.inj_ptr);
             const int32_t *hsp = reinterpret_cast<const int32_t *>(T.blob.data() + T.smp_ptr);
+            // sources of each tile's extended region (tile plus the halo whose
+            // u^{n+1} the two-step kernel computes), x relative to its origin
+            std::vector<std::vector<PtEntry>> xt(two_cap ? geo[i].ntiles : 0);
+            if (two_cap) {
+                const fd_problem &pr = p->prob;
+                const float sc = (float)(pr.dt * pr.dt / std::pow(pr.h, pr.dim));
+                const int ntx = geo[i].tiles_x, ntz = geo[i].ntiles / ntx;
+                for (int k = 0; k < sh.nsrc; ++k) {
+                    const int64_t z = sh.src_idx[k] / pr.n[2] + pr.nb, x = sh.src_idx[k] % pr.n[2] + pr.nb;
+                    for (int tz = 0; tz < ntz; ++tz)
+                        for (int tx = 0; tx < ntx; ++tx) {
+                            const int64_t ex0 = (int64_t)tx * geo[i].tx - g2.hx, ez0 = (int64_t)tz * geo[i].tz - p->st.M;
+                            if (x < ex0 || x >= ex0 + geo[i].tx + 2 * g2.hx || z < ez0 ||
+                                z >= ez0 + geo[i].tz + 2 * p->st.M)
+                                continue;
+                            PtEntry e;
+                            e.z = (int32_t)z;
+                            e.yx = (int32_t)(x - ex0);
+                            e.col = k;
+                            e.scale = sc;
+                            xt[tz * ntx + tx].push_back(e);
+                        }
+                }
+                for (auto &v : xt)
+                    std::stable_sort(v.begin(), v.end(), [](const PtEntry &a, const PtEntry &b) { return a.z < b.z; });
+            }
             for (int t = 0; t < geo[i].ntiles; ++t) {
                 TileRec r;
+                std::memset(&r, 0, sizeof r);
                 r.shot = i;
                 r.tile = t;
+                if (two_cap) {
+                    r.xb = (int)ext.size();
+                    ext.insert(ext.end(), xt[t].begin(), xt[t].end());
+                    r.xe = (int)ext.size();
+                }
                 r.x0 = (t % geo[i].tiles_x) * geo[i].tx;
                 r.z0 = (t / geo[i].tiles_x) * geo[i].tz;
                 r.ib = sh.nsrc ? hip[t] : 0;
@@ -1146,6 +1242,9 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         FDW_CK(cudaMemcpyAsync(t1, recs.data(), ntiles * sizeof(TileRec), cudaMemcpyHostToDevice, s));
         bp.shots = reinterpret_cast<const ShotDesc *>(d);
         bp.tiles = reinterpret_cast<const TileRec *>(t1);
+        if (two_cap && !ext.empty())
+            FDW_CK(cudaMemcpyAsync(xtab, ext.data(), ext.size() * sizeof(PtEntry), cudaMemcpyHostToDevice, s));
+        bp.ext = reinterpret_cast<const PtEntry *>(xtab);
         bp.ntiles = ntiles;
         // shot 0's status word collects the device conditions of the batch
         bp.status = reinterpret_cast<int *>(ws);
@@ -1164,6 +1263,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         key.push_back(reinterpret_cast<uint64_t>(sh.traces_d));
         key.push_back(((uint64_t)(uint32_t)sh.nsrc << 32) | (uint32_t)sh.nrec);
     }
+    key.push_back(two ? 1ull : 0ull);
     key.insert(key.begin(), 2ull);
     cudaGraphExec_t ge = graph_cache_find(key);
     if (!ge) {
@@ -1173,7 +1273,24 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         FDW_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
         cudaError_t ce = cudaSuccess;
         const int nt = p0->prob.nt;
-        for (int n = 0; n < nt && ce == cudaSuccess; ++n) {
+        if (two) {
+            // an odd first step runs alone; then pairs of steps, the outputs
+            // going to the pair of buffers not being read
+            int n = 0, cur = 0, prev = 1;
+            if (nt & 1) {
+                bp.step = 0;
+                ce = launch_batched2d(bv, bp, ntiles, cs);
+                n = 1; cur = 1; prev = 0;
+            }
+            for (; n + 1 < nt && ce == cudaSuccess; n += 2) {
+                const int o1 = cur < 2 ? 2 : 0, o2 = o1 + 1;
+                bp.roles[0] = cur; bp.roles[1] = prev; bp.roles[2] = o1; bp.roles[3] = o2;
+                bp.step = n;
+                ce = launch_batched2d2(bv, bp, ntiles, cs);
+                cur = o2; prev = o1;
+            }
+        }
+        for (int n = 0; n < nt && ce == cudaSuccess && !two; ++n) {
             if (one) {
                 bp.step = n;
                 ce = launch_batched2d(bv, bp, ntiles, cs);

@@ -441,6 +441,260 @@ step2d_batched(const __grid_constant__ BatchParams bp)
 }
 
 // ---------------------------------------------------------------------------
+// Batched shots, two time steps per pass (temporal blocking).  Each tile is
+// staged with the halo that two steps need: u^n with 2M rows (and
+// round4(HX + M) columns) around it, u^{n-1} and kappa with M rows (and HX
+// columns).  The consumers first compute u^{n+1} on the tile plus its M-row
+// halo ("extended region", kept in shared memory; halo points are computed
+// redundantly by every tile that needs them, with the same arithmetic as
+// their owner), then u^{n+2} on the tile from it.  Both results are written
+// to two buffers other than the inputs (four buffers in rotation), so no
+// tile overwrites data another tile still reads.  Per step this moves 10
+// bytes per point through HBM instead of 16.  Outside the grid the staged
+// fields and kappa are zero, so u^{n+1} there is exactly zero, as the
+// boundary condition requires.
+// ---------------------------------------------------------------------------
+template <int M, int R>
+struct Stream2Cfg {
+    static constexpr int TZ = kTZ * R;
+    static constexpr int HX = round4(M);
+    static constexpr int HXC = round4(HX + M);
+    static constexpr int EW = kTX + 2 * HX, EH = TZ + 2 * M;      // extended region
+    static constexpr int CW = kTX + 2 * HXC, CH = TZ + 4 * M;     // u^n box
+    static constexpr int CEL = (CW * CH + 31) & ~31;
+    static constexpr int EEL = (EW * EH + 31) & ~31;
+    static constexpr int SLOT = CEL + 2 * EEL;                    // u^n | u^{n-1} | kappa
+    static constexpr int NB = 2;
+    static constexpr int NCW = kThreads / 32;
+    static constexpr int THREADS = kThreads + 32;
+    static constexpr size_t SMEM = ((size_t)NB * SLOT + EEL) * sizeof(float);
+};
+
+// Barrier of the consumer warps only (named barrier 1; the producer warp does
+// not take part), and the same with an OR over a predicate.
+__device__ __forceinline__ void consumers_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+}
+
+__device__ __forceinline__ bool consumers_any(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kThreads)
+        : "memory");
+    return r != 0;
+}
+
+template <int SHAPE, int M, int R>
+__device__ __forceinline__ void stream2_tile(const BatchView &v, const Staged &st,
+                                             const PtEntry *ext, const float *slot, float *u1,
+                                             float *out1, float *out2, int tid)
+{
+    using C = Stream2Cfg<M, R>;
+    const int x0 = st.rec.x0, z0 = st.rec.z0;
+    const int ex0 = x0 - C::HX, ez0 = z0 - M;            // extended region origin
+    const float *cur = slot, *prv = slot + C::CEL, *kap = slot + C::CEL + C::EEL;
+    // stage 1: u^{n+1} on the extended region (groups of 4 columns)
+    constexpr int GX = C::EW / 4, ITEMS = GX * C::EH;
+#pragma unroll 1
+    for (int it = tid; it < ITEMS; it += kThreads) {
+        const int gx = it % GX, rz = it / GX;
+        const int c0 = 4 * gx;
+        const int zg = ez0 + rz;
+        float cc[4], lap[4];
+        lap2d_at<SHAPE, M, 0, C::CW>(v, cur, rz + M, c0 + (C::HXC - C::HX), cc, lap);
+        const float4 up = ld4(prv + rz * C::EW + c0);
+        const float4 kp = ld4(kap + rz * C::EW + c0);
+        const float uu[4] = {up.x, up.y, up.z, up.w};
+        const float kk[4] = {kp.x, kp.y, kp.z, kp.w};
+        const float d2z = layer_d2(zg, v.phys_lo[2], v.phys_hi[2]);
+        float o[4], g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            g[j] = v.gcoef * (layer_d2(ex0 + c0 + j, v.phys_lo[0], v.phys_hi[0]) + d2z);
+            step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
+        }
+        for (int k = st.rec.xb; k < st.rec.xe; ++k) {
+            const PtEntry en = ext[k];
+            const int xl = en.yx & 0xffff;
+            if (en.z != zg || (xl >> 2) != gx) continue;
+            const float a = en.scale * v.inj_series[(int64_t)v.step * v.inj_ncol + en.col];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (jj == (xl & 3)) o[jj] += a;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+        *reinterpret_cast<float4 *>(u1 + rz * C::EW + c0) = make_float4(o[0], o[1], o[2], o[3]);
+        // points of the tile itself: store and sample step n
+        const int tr = rz - M, tc = c0 - C::HX;
+        if (tr < 0 || tr >= C::TZ || tc < 0 || tc >= kTX) continue;
+        if (st.rec.sb < st.rec.se)
+            for_row(v.smp, st.rec.sb, st.rec.se, zg, tc >> 2, [&](int j, const PtEntry &en) {
+                float sv = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj == j) sv = o[jj];
+                v.smp_out[(int64_t)v.step * v.smp_ncol + en.col] = sv * en.scale;
+            });
+        const int xg = x0 + tc;
+        if (xg < v.nx && zg < v.nz)
+            *reinterpret_cast<float4 *>(out1 + (int64_t)zg * v.pitch + xg) =
+                make_float4(o[0], o[1], o[2], o[3]);
+    }
+    consumers_sync();
+    // stage 2: u^{n+2} on the tile
+    const int tx = tid & 15, ty = tid >> 4;
+    const int xg = x0 + 4 * tx;
+    const bool colok = xg < v.nx;
+    const int step1 = v.step + 1;
+    float d2x[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d2x[j] = layer_d2(xg + j, v.phys_lo[0], v.phys_hi[0]);
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const int rr = ty * R + r;
+        const int zg = z0 + rr;
+        float cc[4], lap[4];
+        lap2d_at<SHAPE, M, 0, C::EW>(v, u1, rr + M, C::HX + 4 * tx, cc, lap);
+        const float4 up = ld4(cur + (rr + 2 * M) * C::CW + C::HXC + 4 * tx);
+        const float4 kp = ld4(kap + (rr + M) * C::EW + C::HX + 4 * tx);
+        const float uu[4] = {up.x, up.y, up.z, up.w};
+        const float kk[4] = {kp.x, kp.y, kp.z, kp.w};
+        const float d2z = layer_d2(zg, v.phys_lo[2], v.phys_hi[2]);
+        float o[4], g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            g[j] = v.gcoef * (d2x[j] + d2z);
+            step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
+        }
+        for (int k = st.rec.xb; k < st.rec.xe; ++k) {
+            const PtEntry en = ext[k];
+            const int xl = (en.yx & 0xffff) - C::HX;
+            if (en.z != zg || xl < 0 || (xl >> 2) != tx) continue;
+            const float a = en.scale * v.inj_series[(int64_t)step1 * v.inj_ncol + en.col];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (jj == (xl & 3)) o[jj] += a;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+        if (st.rec.sb < st.rec.se)
+            for_row(v.smp, st.rec.sb, st.rec.se, zg, tx, [&](int j, const PtEntry &en) {
+                float sv = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj == j) sv = o[jj];
+                v.smp_out[(int64_t)step1 * v.smp_ncol + en.col] = sv * en.scale;
+            });
+        if (!colok || zg >= v.nz) continue;
+        *reinterpret_cast<float4 *>(out2 + (int64_t)zg * v.pitch + xg) =
+            make_float4(o[0], o[1], o[2], o[3]);
+    }
+    consumers_sync();   // u1 is rewritten by the next tile
+}
+
+template <int SHAPE, int M, int R>
+__global__ void __launch_bounds__(Stream2Cfg<M, R>::THREADS)
+step2d_batched2(const __grid_constant__ BatchParams bp)
+{
+    using C = Stream2Cfg<M, R>;
+    constexpr int NB = C::NB;
+    constexpr uint32_t BYTES = (C::CW * C::CH + 2 * C::EW * C::EH) * 4;
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t full[NB], empty[NB];
+    __shared__ Staged staged[NB];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < NB; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], C::NCW);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int G = gridDim.x;
+    const int rc = bp.roles[0], rp = bp.roles[1];
+
+    if (warp == C::NCW) {   // producer: lane 0 waits and issues, the warp copies
+        volatile int *abort_v = &abort_flag;
+        constexpr int kWords = sizeof(ShotInfo) / 4;
+        int i = 0;
+        TileRec next = blockIdx.x < bp.ntiles ? bp.tiles[blockIdx.x] : TileRec{};
+        for (int g = blockIdx.x; g < bp.ntiles; g += G, ++i) {
+            const int b = i % NB;
+            const TileRec rec = next;
+            if (g + G < bp.ntiles) next = bp.tiles[g + G];
+            int go = 1;
+            if (lane == 0) {
+                if (i >= NB && !mbar_wait_bounded(&empty[b], (uint32_t)((i / NB - 1) & 1))) {
+                    atomicOr(bp.status, kStatusTimeout);
+                    *abort_v = 1;
+                }
+                go = !*abort_v;
+            }
+            if (!__shfl_sync(0xffffffffu, go, 0)) break;
+            const ShotDesc &d = bp.shots[rec.shot];
+            if (lane == 0) {
+                float *fd = sm + b * C::SLOT;
+                mbar_expect_tx(&full[b], BYTES);
+                tma_load_2d(fd, &d.c2[rc], &full[b], rec.x0 - C::HXC, rec.z0 - 2 * M);
+                tma_load_2d(fd + C::CEL, &d.p2[rp], &full[b], rec.x0 - C::HX, rec.z0 - M);
+                tma_load_2d(fd + C::CEL + C::EEL, &d.k2, &full[b], rec.x0 - C::HX, rec.z0 - M);
+                staged[b].rec = rec;
+            }
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(&d.info);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&staged[b].info);
+            for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                mbar_arrive(&full[b]);
+            }
+        }
+        if (lane == 0 && *abort_v) {
+            for (int j = i > NB ? i - NB : 0; j < i; ++j)
+                mbar_wait_bounded(&full[j % NB], (j / NB) & 1, 100000000LL);
+        }
+        return;
+    }
+
+    float *u1 = sm + NB * C::SLOT;
+    bool ok = true;
+    int i = 0;
+    for (int g = blockIdx.x; g < bp.ntiles; g += G, ++i) {
+        const int b = i % NB;
+        ok = mbar_wait_bounded(&full[b], (i / NB) & 1);
+        // every consumer warp takes part in the named barriers of a tile, so
+        // they decide together whether to go on (each wait above is bounded)
+        if (consumers_any(!ok || *reinterpret_cast<volatile int *>(&abort_flag))) {
+            ok = false;
+            break;
+        }
+        const Staged &st = staged[b];
+        const BatchView v(st.info, bp);
+        stream2_tile<SHAPE, M, R>(v, st, bp.ext, sm + b * C::SLOT, u1, st.info.buf[bp.roles[2]],
+                                  st.info.buf[bp.roles[3]], tid);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
+    }
+    if (!ok) {
+        atomicOr(bp.status, kStatusTimeout);
+        *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Persistent time loop for small grids (fields resident in L2), where the
 // latency of one launch per step dominates: a cooperative launch keeps every
 // CTA resident; CTAs loop over the time steps and take their tiles of each
@@ -752,6 +1006,57 @@ cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles
         return e;
     const int grid = std::min(ntiles, std::max(1, per_sm) * sms);
     fn<<<grid, v.threads, v.smem, s>>>(bp);
+    return cudaGetLastError();
+}
+
+using Batch2Fn = void (*)(const BatchParams);
+
+Batch2Fn lookup_batched2(int shape, int M)
+{
+    if (shape == FD_CROSS && M == 2) return step2d_batched2<FD_CROSS, 2, 2>;
+    if (shape == FD_CROSS && M == 4) return step2d_batched2<FD_CROSS, 4, 2>;
+    return nullptr;
+}
+
+template <int M>
+void fill_geo2(Batch2Geo *g, size_t *smem)
+{
+    using C = Stream2Cfg<M, 2>;
+    g->tz = C::TZ;
+    g->hx = C::HX;
+    g->hxc = C::HXC;
+    g->cbox[0] = C::CW; g->cbox[1] = C::CH;
+    g->pbox[0] = C::EW; g->pbox[1] = C::EH;
+    *smem = C::SMEM;
+}
+
+int batch2d2_geometry(int shape, int M, Batch2Geo *g)
+{
+    if (!lookup_batched2(shape, M)) return FD_ERR_UNSUPPORTED;
+    size_t smem;
+    if (M == 2) fill_geo2<2>(g, &smem);
+    else fill_geo2<4>(g, &smem);
+    return FD_OK;
+}
+
+cudaError_t launch_batched2d2(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s)
+{
+    Batch2Fn fn = lookup_batched2(v.shape, v.M);
+    if (!fn) return cudaErrorInvalidValue;
+    Batch2Geo g;
+    size_t smem = 0;
+    if (v.M == 2) fill_geo2<2>(&g, &smem);
+    else fill_geo2<4>(&g, &smem);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (ntiles <= 0) return cudaSuccess;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads + 32, smem)) != cudaSuccess)
+        return e;
+    const int grid = std::min(ntiles, std::max(1, per_sm) * sms);
+    fn<<<grid, kThreads + 32, smem, s>>>(bp);
     return cudaGetLastError();
 }
 

@@ -82,6 +82,24 @@ def test_batched_2d_matches_single_shot_and_oracle(M, scheme):
     assert rel_l2(outs[0][-1], otr) < 1e-4
 
 
+@pytest.mark.parametrize("nt", [121, 2, 3])
+def test_batched_two_step_odd_and_short_runs(nt, monkeypatch):
+    """Cross(2) and Cross(4) batches advance two steps per pass (an odd first
+    step runs alone); traces equal single-shot runs and the one-step pass
+    bitwise, for odd, minimal and short step counts."""
+    for M in (4, 2):
+        cases = _shots(M, "spatte", nt=nt)
+        two = _batched(cases)[0]
+        monkeypatch.setenv("FDWAVE_BATCH_2STEP", "0")
+        one = _batched(cases)[0]
+        monkeypatch.delenv("FDWAVE_BATCH_2STEP")
+        for i, c in enumerate(cases):
+            tr, _, rc = c.gpu_forward()
+            assert rc == 0
+            assert np.array_equal(two[i], tr), (M, nt, i, rel_l2(two[i], tr))
+            assert np.array_equal(one[i], tr), (M, nt, i)
+
+
 def test_batched_3d_per_shot_launches():
     cases = _shots(4, "spatte", dim=3, nt=50)
     outs = _batched(cases)
