@@ -1015,13 +1015,15 @@ size_t batch_extra_bytes(int nshots, const fd_shot *shots, int64_t ntiles, bool 
 }
 
 // The two-step kernel applies to single-launch batches of its stencils with at
-// least two steps (FDWAVE_BATCH_2STEP=0 turns it off).
+// least two steps, when FDWAVE_BATCH_2STEP=1 (opt-in: on the 48-shot Cross(4)
+// workload it measured 187 Gpts/s against 250 for the one-step kernel, whose
+// pass is not bound by HBM alone).
 bool batch_two_step(const fd_plan *p0, bool one, Batch2Geo *g)
 {
     if (!one || p0->prob.nt < 2 || batch2d2_geometry(p0->shape_eff, p0->st.M, g) != FD_OK)
         return false;
     const char *e = std::getenv("FDWAVE_BATCH_2STEP");
-    return !(e && std::strcmp(e, "0") == 0);
+    return e && std::strcmp(e, "1") == 0;
 }
 
 }  // namespace
@@ -1043,8 +1045,7 @@ extern "C" int fd_forward_batched_workspace_size(int nshots, const fd_shot *shot
         if (one) ntiles += geo[i].ntiles;
     }
     Batch2Geo g2;
-    const bool two = nshots > 0 && one && shots[0].plan->prob.nt >= 2 &&
-                     batch2d2_geometry(shots[0].plan->shape_eff, shots[0].plan->st.M, &g2) == FD_OK;
+    const bool two = nshots > 0 && batch_two_step(shots[0].plan, one, &g2);
     if (one) tot += batch_extra_bytes(nshots, shots, ntiles, two);
     *bytes = tot;
     return FD_OK;
@@ -1072,9 +1073,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
     std::vector<TileGeo> geo;
     const bool one = batch_geometry(nshots, shots, bv, geo);
     Batch2Geo g2;
-    const bool two_cap = one && p0->prob.nt >= 2 &&
-                         batch2d2_geometry(p0->shape_eff, p0->st.M, &g2) == FD_OK;
-    const bool two = two_cap && batch_two_step(p0, one, &g2);
+    const bool two = batch_two_step(p0, one, &g2);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = reinterpret_cast<char *>(ws);
     // extra region (after every shot's slice): descriptors | tile records |
@@ -1089,7 +1088,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
     char *extra = base + shots_bytes;
     char *xbufs = extra + up(nshots * sizeof(ShotDesc)) + up(ntiles_all * sizeof(TileRec));
     char *xtab = xbufs;
-    if (two_cap)
+    if (two)
         for (int i = 0; i < nshots; ++i) xtab += 2 * up(shots[i].plan->field * sizeof(float));
     std::vector<PtEntry> ext;
     std::vector<StepParams> sps(one ? 0 : nshots);
@@ -1134,7 +1133,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
             r = r ? r : encode_field_map(p, &d.ktile, kap, true);
             p->var = keep;
             if (r) return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-            if (two_cap) {
+            if (two) {
                 float *f2 = reinterpret_cast<float *>(xbufs);
                 float *f3 = reinterpret_cast<float *>(xbufs + up(p->field * sizeof(float)));
                 xbufs += 2 * up(p->field * sizeof(float));
@@ -1174,8 +1173,8 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
             const int32_t *hsp = reinterpret_cast<const int32_t *>(T.blob.data() + T.smp_ptr);
             // sources of each tile's extended region (tile plus the halo whose
             // u^{n+1} the two-step kernel computes), x relative to its origin
-            std::vector<std::vector<PtEntry>> xt(two_cap ? geo[i].ntiles : 0);
-            if (two_cap) {
+            std::vector<std::vector<PtEntry>> xt(two ? geo[i].ntiles : 0);
+            if (two) {
                 const fd_problem &pr = p->prob;
                 const float sc = (float)(pr.dt * pr.dt / std::pow(pr.h, pr.dim));
                 const int ntx = geo[i].tiles_x, ntz = geo[i].ntiles / ntx;
@@ -1203,7 +1202,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
                 std::memset(&r, 0, sizeof r);
                 r.shot = i;
                 r.tile = t;
-                if (two_cap) {
+                if (two) {
                     r.xb = (int)ext.size();
                     ext.insert(ext.end(), xt[t].begin(), xt[t].end());
                     r.xe = (int)ext.size();
@@ -1242,7 +1241,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         FDW_CK(cudaMemcpyAsync(t1, recs.data(), ntiles * sizeof(TileRec), cudaMemcpyHostToDevice, s));
         bp.shots = reinterpret_cast<const ShotDesc *>(d);
         bp.tiles = reinterpret_cast<const TileRec *>(t1);
-        if (two_cap && !ext.empty())
+        if (two && !ext.empty())
             FDW_CK(cudaMemcpyAsync(xtab, ext.data(), ext.size() * sizeof(PtEntry), cudaMemcpyHostToDevice, s));
         bp.ext = reinterpret_cast<const PtEntry *>(xtab);
         bp.ntiles = ntiles;

@@ -84,15 +84,16 @@ def test_batched_2d_matches_single_shot_and_oracle(M, scheme):
 
 @pytest.mark.parametrize("nt", [121, 2, 3])
 def test_batched_two_step_odd_and_short_runs(nt, monkeypatch):
-    """Cross(2) and Cross(4) batches advance two steps per pass (an odd first
-    step runs alone); traces equal single-shot runs and the one-step pass
-    bitwise, for odd, minimal and short step counts."""
+    """With FDWAVE_BATCH_2STEP=1, Cross(2) and Cross(4) batches advance two
+    steps per pass (an odd first step runs alone); traces equal single-shot
+    runs and the one-step pass bitwise, for odd, minimal and short step
+    counts."""
     for M in (4, 2):
         cases = _shots(M, "spatte", nt=nt)
+        monkeypatch.setenv("FDWAVE_BATCH_2STEP", "1")
         two = _batched(cases)[0]
-        monkeypatch.setenv("FDWAVE_BATCH_2STEP", "0")
-        one = _batched(cases)[0]
         monkeypatch.delenv("FDWAVE_BATCH_2STEP")
+        one = _batched(cases)[0]
         for i, c in enumerate(cases):
             tr, _, rc = c.gpu_forward()
             assert rc == 0
