@@ -291,10 +291,11 @@ struct StreamCfg {
     static constexpr int AEL = (SW * SH + 31) & ~31;   // halo box, 128-byte padded
     static constexpr int TEL = kTX * kTZ * R;          // one tile
     static constexpr int SLOT = AEL + 2 * TEL;         // halo box | u_prev tile | kappa tile
-    // as many slots (2 to 4) as fit in about 110 KB, so that two CTAs share an
-    // SM and each keeps up to NB - 1 tiles of copies in flight
-    static constexpr int NB = 110 * 1024 / (SLOT * 4) < 2 ? 2
-                            : 110 * 1024 / (SLOT * 4) > 4 ? 4 : 110 * 1024 / (SLOT * 4);
+    // as many slots (2 to 4) as fit in about 74 KB, so that three CTAs share
+    // an SM (their registers allow three) and each keeps up to NB - 1 tiles of
+    // copies in flight
+    static constexpr int NB = 74 * 1024 / (SLOT * 4) < 2 ? 2
+                            : 74 * 1024 / (SLOT * 4) > 4 ? 4 : 74 * 1024 / (SLOT * 4);
     static constexpr size_t SMEM = (size_t)NB * SLOT * sizeof(float);
     static constexpr int NCW = kThreads / 32;          // consumer warps
     static constexpr int THREADS = kThreads + 32;
