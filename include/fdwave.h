@@ -297,6 +297,42 @@ int fd_forward_noalloc(fd_plan *plan, int model_kind, const float *model_d,
                        int nrec, const int64_t *rec_idx, float *traces_d,
                        const float *state_in_d, float *state_out_d, void *stream);
 
+/*
+ * Evaluation metrics (Section 2.4 and Appendix A), computed on the GPU in
+ * FP64 from FP32 data.  All pointers are DEVICE pointers the caller owns;
+ * the calls are asynchronous on `stream` and allocate nothing.
+ *
+ * fd_error_norms - classical error norms of a numerical data object against a
+ * reference (Eqs. snapnorm1, snapnorm2, snapnormmax): out_d[3] = (scale1 *
+ * sum |num - ref|, scale2 * sqrt(sum (num - ref)^2), max |num - ref|) over n
+ * values.  A 2D snapshot takes scale1 = 1/h^2, scale2 = 1/h; traces and
+ * receiver gathers take the paper's analogous factors with tau for h.
+ * Errors: FD_ERR_ARG, FD_ERR_CUDA.
+ */
+int fd_error_norms(const float *num_d, const float *ref_d, int64_t n, double scale1,
+                   double scale2, double *out_d, void *stream);
+
+/*
+ * fd_dft_gamma - DFT dispersion metric of Appendix A for nrec traces of nt
+ * samples, numerical against reference, both [nt][nrec] like the traces of
+ * fd_forward:
+ *   spec_num_d, spec_ref_d  out [nrec][nfreq] complex (re, im) DFT
+ *                 coefficients A_k, k < nfreq (Eq. dft); 16-byte aligned
+ *   gamma_d       out [nrec][nfreq] gamma_k (Eq. gammadft), or NULL: phase
+ *                 difference num - ref brought into [-pi, pi] by one 2 pi
+ *                 shift (Eq. phasesdifdftajusted), over pi, times |A_k^num|
+ *                 over the trace's largest |A_k^num|; 0 for a zero trace
+ *   norm_d        out [nrec] sqrt(mean_k gamma_k^2) (Eq. norm2gammastdft,
+ *                 averaged over the nfreq frequencies computed)
+ *   agg_d         out [2] (average, maximum) of norm_d over the receivers
+ *                 (Eqs. norm2gammarecdftavg, norm2gammarecdftmax), or NULL
+ * 1 <= nfreq <= nt (nt/2 + 1 covers the frequencies of a real trace).
+ * Errors: FD_ERR_ARG, FD_ERR_CUDA.
+ */
+int fd_dft_gamma(const float *num_d, const float *ref_d, int nt, int nrec, int nfreq,
+                 double *spec_num_d, double *spec_ref_d, float *gamma_d, double *norm_d,
+                 double *agg_d, void *stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char *fd_last_error(void);
 

@@ -73,6 +73,8 @@ class FdError(RuntimeError):
 _lib = None
 _P, _I, _I64, _D, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
 _SIGS = {
+    "fd_error_norms": (_I, [_P, _P, _I64, _D, _D, _P, _P]),
+    "fd_dft_gamma": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
     "fd_weights": (_I, [_P, _I, _P, _P, _P, _P]),
     "fd_cfl_limit": (_I, [_P, _P]),
     "fd_ricker": (_I, [_D, _D, _I, _P]),
@@ -275,6 +277,39 @@ def fd_forward_noalloc(plan: Plan, model, src_idx: np.ndarray, wavelet, rec_idx:
 
 def fd_status_read(plan: Plan, ws, stream=None) -> int:
     return lib().fd_status_read(plan.ptr, _addr(ws), _stream_ptr(stream))
+
+
+def fd_error_norms(num, ref, scale1: float = 1.0, scale2: float = 1.0, out=None, stream=None):
+    """(scale1 sum|num - ref|, scale2 sqrt(sum (num - ref)^2), max|num - ref|) as a
+    float64 device tensor [3] (Section 2.4); num and ref are float32 device
+    tensors of the same size."""
+    import torch
+    assert num.dtype == torch.float32 and ref.dtype == torch.float32 and num.numel() == ref.numel()
+    out = torch.empty(3, dtype=torch.float64, device=num.device) if out is None else out
+    _check(lib().fd_error_norms(_addr(num), _addr(ref), num.numel(), scale1, scale2, _addr(out),
+                                _stream_ptr(stream)))
+    return out
+
+
+def fd_dft_gamma(num, ref, nfreq: int = 0, with_gamma: bool = True, stream=None):
+    """DFT dispersion metric of Appendix A for traces num, ref [nt, nrec]
+    (float32 device tensors).  Returns (gamma [nrec, nfreq] float32 or None,
+    trace norms [nrec] float64, (average, maximum) float64 [2], and the two
+    spectra [nrec, nfreq, 2] float64); nfreq defaults to nt // 2 + 1."""
+    import torch
+    nt, nrec = num.shape
+    assert ref.shape == num.shape and num.dtype == torch.float32 and ref.dtype == torch.float32
+    nfreq = nfreq or nt // 2 + 1
+    dev = num.device
+    sn = torch.empty((nrec, nfreq, 2), dtype=torch.float64, device=dev)
+    sr = torch.empty_like(sn)
+    g = torch.empty((nrec, nfreq), dtype=torch.float32, device=dev) if with_gamma else None
+    norms = torch.empty(nrec, dtype=torch.float64, device=dev)
+    agg = torch.empty(2, dtype=torch.float64, device=dev)
+    _check(lib().fd_dft_gamma(_addr(num), _addr(ref), nt, nrec, nfreq, _addr(sn), _addr(sr),
+                              _addr(g) if g is not None else None, _addr(norms), _addr(agg),
+                              _stream_ptr(stream)))
+    return g, norms, agg, (sn, sr)
 
 
 def fd_adjoint_gradient(plan: Plan, model, src_idx, wavelet, rec_idx, resid, k: int, grad, ws,

@@ -18,7 +18,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["weights.cpp", "plan.cu", "aux.cu", "step2d.cu", "step3d.cu", "noalloc.cu"]
+SOURCES = ["weights.cpp", "plan.cu", "aux.cu", "step2d.cu", "step3d.cu", "noalloc.cu", "metrics.cu"]
 
 
 def _deps_mtime() -> float:
