@@ -41,9 +41,10 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=400, help="physical nodes per axis")
     ap.add_argument("--nt", type=int, default=1500)
-    ap.add_argument("--workload", default="3d", choices=["3d", "2d", "batched", "fwi"],
+    ap.add_argument("--workload", default="3d", choices=["3d", "2d", "batched", "fwi", "metrics"],
                     help="3d: 400^3 forward (default); 2d: 1001^2 x 18 stencils; batched: "
-                         "48 2D shots on three grids; fwi: 256^3 gradient, 16 shots")
+                         "48 2D shots on three grids; fwi: 256^3 gradient, 16 shots; metrics: "
+                         "DFT dispersion metric of a 2000-sample x 1001-receiver gather pair")
     ap.add_argument("--shots", type=int, default=0, help="fwi/batched: use the first N shots")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -462,6 +463,50 @@ def run_other(args):
         dist.destroy_process_group()
 
 
+def run_metrics(args):
+    """Appendix A's DFT dispersion metric (fd_dft_gamma) on a pair of gathers of
+    the 1001^2 workload's receiver size (2000 samples x 1001 receivers, all
+    nt/2 + 1 frequencies): numerical = reference delayed by two samples plus
+    noise.  Metric: complex multiply-adds of the two direct DFTs per second."""
+    import torch
+    import paper_2606_04882_gb300 as F
+    dev = torch.device("cuda")
+    nt, nrec = 2000, 1001
+    nfreq = nt // 2 + 1
+    g = torch.Generator(dev).manual_seed(11)
+    ref = (torch.randn((nt, nrec), device=dev, generator=g).cumsum(0) * 1e-2).contiguous()
+    num = (torch.roll(ref, 2, 0) + 1e-3 * torch.randn((nt, nrec), device=dev, generator=g)).contiguous()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        F.fd_dft_gamma(num, ref)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        _, _, agg, _ = F.fd_dft_gamma(num, ref)
+    b.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = a.elapsed_time(b) / args.steps
+    macs = 2.0 * nt * nrec * nfreq
+    value = macs / (ms * 1e-3) / 1e9
+    # per sample: 2 FMAs (accumulate) + 4 multiplies and 2 adds (twiddle rotation)
+    gflops = 8.0 * macs / (ms * 1e-3) / 1e9
+    out = {"metric": "DFT dispersion metric: complex multiply-adds per second (2 x 2000 x 1001 x 1001)",
+           "value": value, "unit": "G/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "metrics_dft_gamma 2000 samples x 1001 receivers, 1001 frequencies"},
+           "roofline": {"bound": "alu", "achieved": gflops, "peak": 1250.0, "unit": "GFLOP/s",
+                        "frac": gflops / 1250.0, "traffic": None,
+                        "peak_source": "nominal FP64 rate of a GB300 (not measured)"},
+           "result": {"gamma_norm_avg": float(agg[0]), "gamma_norm_max": float(agg[1])},
+           "clocks": clocks, "gpu_launches": args.steps * 4}
+    print(json.dumps(out))
+
+
 def cpu_baseline(pr, dt, steps=2):
     """The FP64 oracle on a bounded sample: `steps` time steps of the full
     460^3 grid with the Cross(4) stencil on all host cores."""
@@ -525,5 +570,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.workload == "3d":
         run_gpu(a)
+    elif a.workload == "metrics":
+        run_metrics(a)
     else:
         run_other(a)
