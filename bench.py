@@ -365,7 +365,6 @@ def run_other(args):
         dt = 0.5 * F.fd_cfl_limit(F.stencil_desc(3, "cross", 4)) * pr0.h / pr0.vmax
         plan = F.Plan(pr0.shape, pr0.h, dt, pr0.nt, pr0.nb, pr0.vmax, F.stencil_desc(3, "cross", 4))
         m = torch.from_numpy((1.0 / pr0.vel.astype(np.float64) ** 2).astype(np.float32)).to(dev)
-        plan.autotune(m, F.FD_MODEL_SLOWNESS2)                       # untimed tile choice
         ri = plan.linear_index(pr0.rec)
         wav = torch.from_numpy(F.fd_ricker(pr0.f0, dt, pr0.nt)[:, None].copy()).to(dev)
         resid = torch.randn((pr0.nt, len(ri)), device=dev, generator=torch.Generator(dev).manual_seed(5))
