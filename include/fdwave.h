@@ -248,11 +248,19 @@ int fd_adjoint_gradient(fd_plan *plan, int model_kind, const float *model_d,
                         float *wavelet_grad_d, void *ws_d, size_t ws_bytes, void *stream);
 
 /*
- * Batched shots: independent forward problems (possibly on grids of
- * different size, same stencil, dt and nt) advanced together, one launch per
- * time step over a tile table spanning all shots, the whole time loop
- * captured once into a CUDA graph and replayed.  Fields of every shot must
- * fit the workspace at once.
+ * Batched shots (the batching of the paper's many-shot surveys; Section 6
+ * runs one forward problem per source): independent forward problems,
+ * possibly on grids of different size, with the same stencil, dt and nt,
+ * advanced together.  For 2D cross stencils with M = 2, 4, 8 each time step is
+ * one launch of persistent CTAs over a table of every shot's tiles; other
+ * batches launch each shot's step kernel in turn.  The whole time loop is
+ * captured once into a CUDA graph and replayed on repeat calls.  Fields of
+ * every shot must fit the workspace at once.  With the environment variable
+ * FDWAVE_BATCH_2STEP=1, Cross(2) and Cross(4) batches advance two time steps
+ * per pass instead (temporal blocking; two more fields per shot in the
+ * workspace, same results bit for bit).
+ * fd_forward_batched: traces only (no final states).  Errors: FD_ERR_ARG
+ * (shots that differ in dim, stencil, dt or nt), FD_ERR_NOMEM, FD_ERR_CUDA.
  */
 typedef struct {
     const fd_plan *plan;      /* plan of this shot's grid (shared stencil/dt/nt) */
