@@ -248,10 +248,9 @@ int fd_adjoint_gradient(fd_plan *plan, int model_kind, const float *model_d,
                         float *wavelet_grad_d, void *ws_d, size_t ws_bytes, void *stream);
 
 /*
- * Batched shots (the batching of the paper's many-shot surveys; Section 6
- * runs one forward problem per source): independent forward problems,
- * possibly on grids of different size, with the same stencil, dt and nt,
- * advanced together.  For 2D cross stencils with M = 2, 4, 8 each time step is
+ * Batched shots (no counterpart in the paper, whose experiments run one
+ * source at a time): independent forward problems, possibly on grids of
+ * different size, with the same stencil, dt and nt, advanced together.  For 2D cross stencils with M = 2, 4, 8 each time step is
  * one launch of persistent CTAs over a table of every shot's tiles; other
  * batches launch each shot's step kernel in turn.  The whole time loop is
  * captured once into a CUDA graph and replayed on repeat calls.  Fields of
