@@ -216,10 +216,10 @@ step3d_cross(const __grid_constant__ StepParams p)
     // Queue of centre values as packed pairs (x, y) and (z, w).  Unrolled
     // (M <= 4): the plane fed at stream index s sits in slot s mod QL and the
     // loop is unrolled by QL.  Blocked (M >= 6, to keep the code small): the
-    // loop is unrolled by UF = 4 over a queue of QL + 3 slots that moves down
+    // loop is unrolled by UF = 3 over a queue of QL + 2 slots that moves down
     // UF slots at the start of each block; sub-step uu feeds slot QL-1+uu.
     constexpr bool kUnroll = M <= 4;
-    constexpr int UF = kUnroll ? QL : 4;
+    constexpr int UF = kUnroll ? QL : 3;
     constexpr int QN = kUnroll ? QL : QL + UF - 1;
     f32x2 qa[QN], qb[QN];
 #pragma unroll
@@ -451,7 +451,7 @@ step3d_planar(const __grid_constant__ StepParams p)
     // of a block of UF planes (i = 0..2M); at the start of each block the
     // accumulators move down UF slots and the top UF slots (outputs that start
     // in this block) are cleared
-    constexpr int UF = 2;
+    constexpr int UF = 3;
     constexpr int AN = QL + UF - 1;
     f32x2 acc[AN][2];
 #pragma unroll
