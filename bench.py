@@ -554,8 +554,9 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": el * 1e3 / max(args.steps, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": "3d_gradient_random_%d (%d^3 padded), stencils cross4,cross8,rhombus4"
-                                  % (args.n, setups[0].pshape[0])},
+           "config": {"workload": "3d_gradient_random_%d (%d^3 padded), %d steps, stencils %s"
+                                  % (args.n, setups[0].pshape[0], args.nt,
+                                     ",".join("%s%d_%s" % st for st in STENCILS))},
            "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": threads, "kind": "oracle",
                             "sample": "one time step of the full padded grid per bench step, "
                                       "cycling through the three stencils"},
