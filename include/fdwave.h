@@ -174,9 +174,11 @@ int fd_plan_get_info(const fd_plan *plan, fd_plan_info *info);
 /*
  * fd_plan_autotune - pick the plan's kernel variant by measurement: each
  * candidate tile shape (rows per thread in 2D; y tile and z-chunk length in
- * 3D) runs 12 steps of this plan's problem on `model_d` with no sources or
- * receivers, three times (best time counts), and the fastest is kept in the
- * plan and in a per-process cache
+ * 3D) is timed per step on this plan's problem on `model_d` with no sources
+ * or receivers (best of three 64-step runs minus best of three 16-step runs,
+ * over 48, as captured graphs); a candidate must be 2 % faster than the best
+ * before it to replace it; the choice is kept in the plan and in a
+ * per-process cache
  * keyed by device name, dimension, shape, M, N and padded size (appended to
  * the file named by the environment variable FDWAVE_TUNE_CACHE, and read
  * from it, when that is set).  Synchronises `stream`.  Results of the plan's

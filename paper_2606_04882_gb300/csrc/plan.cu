@@ -38,6 +38,11 @@ struct fd_plan {
 
 namespace fdw {
 
+// Set while fd_plan_autotune times candidates: their time loops are captured
+// into graphs kept here instead of the shared cache (so that no candidate
+// evicts a caller's graph), and destroyed when tuning ends.
+thread_local std::map<std::vector<uint64_t>, cudaGraphExec_t> *t_tune_graphs = nullptr;
+
 namespace {
 
 thread_local char g_err[512] = "";
@@ -166,8 +171,12 @@ int build_table(const fd_plan *p, const TileGeo &G, int n, const int64_t *idx, f
         int st = locate(p, G, idx[i], i, scale, pts[i]);
         if (st) return st;
     }
+    // by tile, then z, then (y, x): the kernels find a plane's and a thread's
+    // entries by binary search
     std::stable_sort(pts.begin(), pts.end(), [](const Pt &a, const Pt &b) {
-        return a.tile != b.tile ? a.tile < b.tile : a.e.z < b.e.z;
+        if (a.tile != b.tile) return a.tile < b.tile;
+        if (a.e.z != b.e.z) return a.e.z < b.e.z;
+        return (uint32_t)a.e.yx < (uint32_t)b.e.yx;
     });
     ptr.assign(G.ntiles + 1, 0);
     for (auto &q : pts) ptr[q.tile + 1]++;
@@ -562,28 +571,51 @@ extern "C" int fd_plan_autotune(fd_plan *p, int model_kind, const float *model, 
     FDW_CK(cudaEventCreate(&e1));
     float best = 1e30f;
     TuneChoice bestc = cands[0];
-    for (const TuneChoice &c : cands) {
-        fd_plan q = *p;
-        if (apply_choice(&q, c)) continue;
-        q.prob.nt = 12;
-        if (make_layout(&q, 0, 0, false, 1).total > ws_bytes) continue;
-        st = fd_forward(&q, model_kind, model, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr,
-                        nullptr, ws, ws_bytes, stream);
-        if (st) break;
-        // best of three timed runs: single runs of a few steps are noisy
-        float ms = 1e30f;
-        for (int r = 0; r < 3 && !st; ++r) {
+    // Time per step of a candidate: (best of three 64-step runs - best of three
+    // 16-step runs) / 48, both run as captured graphs like a caller's long
+    // runs, which leaves out the set-up of each call (kappa, tables) and the
+    // first steps' ramp.
+    struct Tuning {
+        std::map<std::vector<uint64_t>, cudaGraphExec_t> graphs;
+        cudaStream_t s;
+        explicit Tuning(cudaStream_t st) : s(st) { t_tune_graphs = &graphs; }
+        ~Tuning()
+        {
+            t_tune_graphs = nullptr;
+            cudaStreamSynchronize(s);
+            for (auto &g : graphs) cudaGraphExecDestroy(g.second);
+        }
+    } tuning(s);
+    auto timed = [&](fd_plan &q, int nt, float &out) -> int {
+        q.prob.nt = nt;
+        out = 1e30f;
+        for (int r = 0; r < 3; ++r) {
             FDW_CK(cudaEventRecord(e0, s));
-            st = fd_forward(&q, model_kind, model, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr,
-                            nullptr, ws, ws_bytes, stream);
+            const int rs = fd_forward(&q, model_kind, model, 0, nullptr, nullptr, 0, nullptr, nullptr,
+                                      nullptr, nullptr, ws, ws_bytes, stream);
+            if (rs) return rs;
             FDW_CK(cudaEventRecord(e1, s));
             FDW_CK(cudaEventSynchronize(e1));
             float t = 0.f;
             FDW_CK(cudaEventElapsedTime(&t, e0, e1));
-            ms = std::min(ms, t);
+            out = std::min(out, t);
         }
+        return FD_OK;
+    };
+    for (const TuneChoice &c : cands) {
+        fd_plan q = *p;
+        if (apply_choice(&q, c)) continue;
+        q.prob.nt = 64;
+        if (make_layout(&q, 0, 0, false, 1).total > ws_bytes) continue;
+        st = fd_forward(&q, model_kind, model, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr,
+                        nullptr, ws, ws_bytes, stream);     // warm-up
         if (st) break;
-        if (ms < best) {
+        float t64 = 0.f, t16 = 0.f;
+        if ((st = timed(q, 64, t64)) || (st = timed(q, 16, t16))) break;
+        const float ms = (t64 - t16) / 48.f;
+        // a later candidate must win by 2 %: the first of each tile shape is
+        // the cost model's z-chunk, and near-ties are timing noise
+        if (ms < 0.98f * best) {
             best = ms;
             bestc = c;
         }
@@ -810,7 +842,13 @@ extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int ns
             ((uint64_t)(uint32_t)nsrc << 32) | (uint32_t)nrec, (uint64_t)p->prob.nt,
             ((uint64_t)p->var.tz << 32) | (uint32_t)p->zchunk,
             ((uint64_t)p->var.threads << 32) | (uint32_t)p->var.generic};
-        cudaGraphExec_t ge = graph_cache_find(key);
+        cudaGraphExec_t ge = nullptr;
+        if (t_tune_graphs) {
+            auto it = t_tune_graphs->find(key);
+            if (it != t_tune_graphs->end()) ge = it->second;
+        } else {
+            ge = graph_cache_find(key);
+        }
         if (!ge) {
             cudaStream_t cs;
             FDW_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -827,7 +865,8 @@ extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int ns
             const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
             cudaGraphDestroy(g);
             if (ie != cudaSuccess) return set_error(FD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
-            graph_cache_put(key, ge);
+            if (t_tune_graphs) (*t_tune_graphs)[key] = ge;
+            else graph_cache_put(key, ge);
         }
         FDW_CK(cudaGraphLaunch(ge, s));
     } else {

@@ -36,18 +36,38 @@ __host__ __device__ constexpr int ring_depth(int slot_floats, int ctas)
     return n < 4 ? 4 : n > 8 ? 8 : n;
 }
 
-// Tile table walk for one plane: apply f(j, entry) to owned entries with
-// entry.z == z; `k` advances past them (entries are z-sorted per tile).
+// Tile table walk for one plane: apply f(j, entry) to this thread's entries
+// with entry.z == z.  Entries are sorted by (z, y, x) within a tile, so the
+// plane's segment and, inside it, this thread's row and 4 columns are found
+// by binary search; `k` advances to the first entry of a later plane.
+__device__ __forceinline__ long long entry_key(int z, int yx)
+{
+    return ((long long)z << 32) | (unsigned)yx;
+}
+
+__device__ __forceinline__ int first_at_least(const PtEntry *tab, int lo, int hi, long long key)
+{
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (entry_key(tab[mid].z, tab[mid].yx) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <class F>
 __device__ __forceinline__ void plane_entries(const PtEntry *tab, int &k, int kend, int z,
                                               int tx, int ty, F f)
 {
-    while (k < kend && tab[k].z < z) ++k;
-    for (; k < kend && tab[k].z == z; ++k) {
-        const PtEntry en = tab[k];
-        const int xl = en.yx & 0xffff, yl = en.yx >> 16;
-        if (yl == ty && (xl >> 2) == tx) f(xl & 3, en);
+    const int zb = first_at_least(tab, k, kend, entry_key(z, 0));
+    const int ze = first_at_least(tab, zb, kend, entry_key(z + 1, 0));
+    const int lo = (ty << 16) | (4 * tx), hi = lo + 4;
+    for (int i = first_at_least(tab, zb, ze, entry_key(z, lo)); i < ze; ++i) {
+        const PtEntry en = tab[i];
+        if (en.yx >= hi) break;
+        f(en.yx & 3, en);
     }
+    k = ze;
 }
 
 // Out-of-line handlers for the (rare) planes that carry table entries, so the
