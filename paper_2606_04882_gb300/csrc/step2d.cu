@@ -20,18 +20,37 @@ constexpr int kTX = 64;     // output columns per tile
 constexpr int kTZ = 16;     // thread rows per tile
 constexpr int kThreads = 256;
 
-// Visit the tile's table entries owned by this thread: f(r, j, entry).
-template <int R, class F>
-__device__ __forceinline__ void for_owned(const int32_t *ptr, const PtEntry *tab, int tile,
-                                          int z0, int tx, int ty, F f)
+// Point tables hold each tile's entries sorted by (z, x): the entries of row
+// zg and thread column tx (x in [4 tx, 4 tx + 4)) are found by binary search
+// in [b, e) and f(j, entry) is applied to each, j = x - 4 tx.
+__device__ __forceinline__ long long entry_key(int z, int x)
 {
-    const int b = ptr[tile], e = ptr[tile + 1];
-    for (int k = b; k < e; ++k) {
-        const PtEntry en = tab[k];
-        const int zl = en.z - z0 - ty * R;
-        const int xl = en.yx & 0xffff;
-        if (zl >= 0 && zl < R && (xl >> 2) == tx) f(zl, xl & 3, en);
+    return ((long long)z << 32) | (unsigned)x;
+}
+
+template <class F>
+__device__ __forceinline__ void for_row(const PtEntry *tab, int b, int e, int zg, int tx, F f)
+{
+    const long long lo = entry_key(zg, 4 * tx), hi = entry_key(zg, 4 * tx + 4);
+    int l = b, h = e;
+    while (l < h) {
+        const int mid = (l + h) >> 1;
+        if (entry_key(tab[mid].z, tab[mid].yx) < lo) l = mid + 1;
+        else h = mid;
     }
+    for (int k = l; k < e; ++k) {
+        const PtEntry en = tab[k];
+        if (entry_key(en.z, en.yx) >= hi) break;
+        f(en.yx & 3, en);
+    }
+}
+
+// The same over a tile's whole range in a CSR table (ptr[tile] .. ptr[tile+1]).
+template <class F>
+__device__ __forceinline__ void for_owned(const int32_t *ptr, const PtEntry *tab, int tile, int zg,
+                                          int tx, F f)
+{
+    for_row(tab, ptr[tile], ptr[tile + 1], zg, tx, f);
 }
 
 // Laplacian sum of 4 consecutive columns col0 .. col0+3 of shared-memory row zl
@@ -185,7 +204,7 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
         }
         // injection inside the bracket; adjoint residuals are scaled by kappa
         if (p.inj_ptr)
-            for_owned<1>(p.inj_ptr, p.inj, tile, z0 + ty * R + r, tx, 0, [&](int, int j, const PtEntry &en) {
+            for_owned(p.inj_ptr, p.inj, tile, z0 + ty * R + r, tx, [&](int j, const PtEntry &en) {
                 float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
                 if (MODE == kModeAdjoint) a *= kk[j];
 #pragma unroll
@@ -196,7 +215,7 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
         for (int j = 0; j < 4; ++j)
             if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
         if (p.smp_ptr)
-            for_owned<1>(p.smp_ptr, p.smp, tile, z0 + ty * R + r, tx, 0, [&](int, int j, const PtEntry &en) {
+            for_owned(p.smp_ptr, p.smp, tile, z0 + ty * R + r, tx, [&](int j, const PtEntry &en) {
                 float v = 0.f;
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
@@ -270,18 +289,6 @@ struct Staged {
     ShotInfo info;
     TileRec rec;
 };
-
-// Apply f(j, entry) to the entries [b, e) of a point table that lie in row zg
-// and in thread column tx.
-template <class F>
-__device__ __forceinline__ void for_row(const PtEntry *tab, int b, int e, int zg, int tx, F f)
-{
-    for (int k = b; k < e; ++k) {
-        const PtEntry en = tab[k];
-        const int xl = en.yx & 0xffff;
-        if (en.z == zg && (xl >> 2) == tx) f(xl & 3, en);
-    }
-}
 
 template <int M, int R>
 struct StreamCfg {
@@ -862,7 +869,7 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
     }
     float4 br = make_float4(o[0], o[1], o[2], o[3]);
     if (p.inj_ptr)
-        for_owned<1>(p.inj_ptr, p.inj, tile, z0, tx, ty, [&](int r, int j, const PtEntry &en) {
+        for_owned(p.inj_ptr, p.inj, tile, z0 + ty, tx, [&](int j, const PtEntry &en) {
             float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
             if (MODE == kModeAdjoint) a *= kk[j];
             add4(br, j, a);
@@ -872,7 +879,7 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
         if (gm[j] != 0.f) o[j] = __fdividef(o[j], 1.f + gm[j]);
     const float4 un = make_float4(o[0], o[1], o[2], o[3]);
     if (p.smp_ptr)
-        for_owned<1>(p.smp_ptr, p.smp, tile, z0, tx, ty, [&](int r, int j, const PtEntry &en) {
+        for_owned(p.smp_ptr, p.smp, tile, z0 + ty, tx, [&](int j, const PtEntry &en) {
             float v = get4(un, j) * en.scale;
             if (MODE == kModeAdjoint) v /= kk[j];
             p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
