@@ -65,8 +65,8 @@ def dist_env():
 TRAFFIC_SOURCES = ("paper_2606_04882_gb300/csrc/step3d.cu",
                    "paper_2606_04882_gb300/csrc/device_common.cuh",
                    "paper_2606_04882_gb300/csrc/internal.h")
-TRAFFIC_DIGEST = "dda02420909c778722f577e45dfad5d16c441e5b3b00edb424ad656b366c2c81"
-TRAFFIC_B_PER_POINT = {"cross4_spatte": 16.619, "cross8_spatte": 16.769, "rhombus4_displs": 16.501}
+TRAFFIC_DIGEST = "67448eafb4897353668d2e5405ca7ccba9db0cceff205e4cc2e03a4842fde978"
+TRAFFIC_B_PER_POINT = {"cross4_spatte": 16.563, "cross8_spatte": 16.408, "rhombus4_displs": 16.592}
 
 
 def traffic_per_launch(stencil, pts):
