@@ -77,3 +77,92 @@ def test_gamma_of_a_time_delay():
     assert np.allclose(g[0][~edge], expect[~edge], atol=1e-9)
     assert np.allclose(np.abs(g[0][edge]), np.abs(expect[edge]), atol=1e-9)
     assert avg == mx
+
+
+# --- wavelet (CWT) dispersion metric -------------------------------------------------
+
+
+def test_cwt_tone_peaks_at_its_matched_scale():
+    """A pure tone on DFT line k1: its wavelet power over the scales peaks at
+    the scale matched to line k1 (the stationary point of the power in s),
+    its envelope is constant in time and its phase advances 2 pi k1 / nt per
+    sample."""
+    nt = 256
+    n = np.arange(nt)
+    for k1, w0 in ((9, 6.0), (23, 6.0), (40, 8.0)):
+        u = np.cos(2 * np.pi * k1 * n / nt + 0.4)[:, None]
+        S = X.cwt(u, 60, w0)[0]
+        power = (np.abs(S) ** 2).mean(axis=1)
+        assert np.argmax(power) == k1
+        env = np.abs(S[k1])
+        assert env.std() < 1e-12 * env.mean()
+        step = np.angle(S[k1, 1:] / S[k1, :-1])
+        assert np.allclose(step, 2 * np.pi * k1 / nt, atol=1e-12)
+        assert np.all(S[0] == 0)
+
+
+def test_cwt_of_an_impulse_has_unit_energy_per_scale():
+    """The normalisation (2 pi s / tau)^(1/2) pi^(-1/4) gives every wavelet unit
+    energy: for a unit impulse, sum_n |S_{n,k}|^2 = 1 at every scale whose
+    Gaussian lies well inside (0, nt/2]."""
+    nt = 1024
+    u = np.zeros((nt, 1))
+    u[0, 0] = 1.0
+    S = X.cwt(u, 120)[0]
+    e = (np.abs(S) ** 2).sum(axis=1)
+    assert np.allclose(e[15:120], 1.0, rtol=1e-6)
+
+
+def test_cwt_of_a_delayed_trace_is_the_delayed_cwt():
+    """Circularly delaying the trace by m samples delays each scale's row by m
+    (this fixes the sign of the inverse transform's exponent)."""
+    rng = np.random.default_rng(7)
+    nt, m = 200, 13
+    u = rng.standard_normal((nt, 3))
+    S = X.cwt(u, 50)
+    Sd = X.cwt(np.roll(u, m, axis=0), 50)
+    assert np.allclose(Sd, np.roll(S, m, axis=2), atol=1e-12 * np.abs(S).max())
+
+
+def test_cwt_rows_hold_only_positive_frequencies():
+    """The Heaviside factor: every scale's row is an analytic signal, with no
+    zero-frequency and no negative-frequency content."""
+    rng = np.random.default_rng(8)
+    nt = 150
+    S = X.cwt(rng.standard_normal((nt, 2)), 40)
+    F = np.fft.fft(S, axis=2)
+    tol = 1e-12 * np.abs(F).max()
+    assert np.abs(F[..., 0]).max() < tol
+    assert np.abs(F[..., nt // 2 + 1:]).max() < tol
+
+
+def test_gamma_w_of_a_phase_shifted_tone():
+    """num = cos(w n + delta), ref = cos(w n), w on DFT line k1: every S^num is
+    e^{i delta} S^ref, so gamma^W = (delta/pi) |S^num| / max |S^num|; it is
+    delta/pi along the matched scale, where the amplitude is largest."""
+    nt, k1 = 128, 11
+    n = np.arange(nt)
+    for delta in (0.5, -2.0, 3.0):
+        num = np.cos(2 * np.pi * k1 * n / nt + delta)[:, None]
+        ref = np.cos(2 * np.pi * k1 * n / nt)[:, None]
+        g, norms, avg, mx, amax = X.cwt_gamma(num, ref, 30)
+        assert np.allclose(g[0, k1], delta / np.pi, atol=1e-12)
+        assert np.abs(g).max() <= abs(delta) / np.pi + 1e-12
+        assert avg == mx == norms[0] > 0
+
+
+def test_gamma_w_wraps_and_vanishes_where_it_should():
+    nt, k1 = 64, 5
+    n = np.arange(nt)
+    num = np.cos(2 * np.pi * k1 * n / nt + 3.0)[:, None]
+    ref = np.cos(2 * np.pi * k1 * n / nt - 3.0)[:, None]
+    g, _, _, _, _ = X.cwt_gamma(num, ref, 12)
+    assert np.allclose(g[0, k1], (6.0 - 2 * np.pi) / np.pi, atol=1e-12)
+    rng = np.random.default_rng(9)
+    u = rng.standard_normal((80, 3))
+    g, norms, avg, mx, amax = X.cwt_gamma(u, u)
+    assert np.all(g == 0) and np.all(norms == 0) and avg == mx == 0 and np.all(amax > 0)
+    z = u.copy()
+    z[:, 1] = 0.0
+    g, norms, _, _, amax = X.cwt_gamma(z, u)
+    assert np.all(g[1] == 0) and norms[1] == 0 and amax[1] == 0
