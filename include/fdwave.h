@@ -342,6 +342,41 @@ int fd_dft_gamma(const float *num_d, const float *ref_d, int nt, int nrec, int n
                  double *spec_num_d, double *spec_ref_d, float *gamma_d, double *norm_d,
                  double *agg_d, void *stream);
 
+/*
+ * fd_cwt_gamma - wavelet (CWT) dispersion metric of Appendix A for nrec traces
+ * of nt samples, numerical against reference, both [nt][nrec].  The printed
+ * transform (Eqs. cwt1, cwt) is read as the DFT-based Morlet transform of
+ * Torrence and Compo that the appendix follows, one inverse DFT:
+ *   S_{n,k} = (1/nt) sum_{k'=1}^{nt/2} A_k' Psi(s_k omega_k') exp(+2 pi i k' n / nt)
+ * with A the DFT of Eq. dft, omega_k' = 2 pi k' / (nt tau) (Eq. omegak; the
+ * Heaviside factor drops k' = 0 and k' > nt/2), Psi(s omega) = (2 pi s / tau)^(1/2)
+ * pi^(-1/4) exp(-(s omega - omega0)^2 / 2) (Eqs. cwt2, cwt3), and scale k >= 1
+ * the one whose Fourier period is DFT line k's: s_k omega_k = (omega0 +
+ * sqrt(2 + omega0^2)) / 2.  Scale 0 has no finite scale: S_{n,0} = 0.  tau
+ * cancels and is not an argument.
+ *   omega0        Morlet centre frequency (> 0; 6 is the usual choice)
+ *   spec_num_d, spec_ref_d  out [nrec][nt/2 + 1] complex DFT lines (re, im)
+ *   cwt_num_d, cwt_ref_d    out [nrec][nscale][nt] complex S_{n,k} (re, im)
+ *   gamma_d       out [nrec][nscale][nt] gamma_{n,k} (Eq. gammacwt), or NULL:
+ *                 wrapped phase difference num - ref (Eqs. phasesdifcwt,
+ *                 phasesdifcwtajusted) over pi, times |S^num_{n,k}| over amax
+ *   amax_d        out [nrec] largest |S^num_{n,k}| of each trace (Eq.
+ *                 amplmaxcwt); gamma is 0 where it is 0
+ *   norm_d        out [nrec] sqrt(mean over n and k of gamma^2) (Eq.
+ *                 norm2gammastcwt)
+ *   agg_d         out [2] (average, maximum) of norm_d (Eqs.
+ *                 norm2gammareccwtavg, norm2gammareccwtmax), or NULL
+ * 1 <= nscale <= nt, 1 <= nrec <= 65535, nt <= 29054 (one trace's DFT lines
+ * are staged in shared memory).  Cost: nrec nscale nt (nt/2) complex
+ * multiply-adds per trace set, in FP64.  All buffers are DEVICE pointers,
+ * 16-byte aligned where complex.
+ * Errors: FD_ERR_ARG, FD_ERR_CUDA.
+ */
+int fd_cwt_gamma(const float *num_d, const float *ref_d, int nt, int nrec, int nscale,
+                 double omega0, double *spec_num_d, double *spec_ref_d, double *cwt_num_d,
+                 double *cwt_ref_d, float *gamma_d, double *amax_d, double *norm_d,
+                 double *agg_d, void *stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char *fd_last_error(void);
 

@@ -75,6 +75,7 @@ _P, _I, _I64, _D, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_
 _SIGS = {
     "fd_error_norms": (_I, [_P, _P, _I64, _D, _D, _P, _P]),
     "fd_dft_gamma": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _P]),
+    "fd_cwt_gamma": (_I, [_P, _P, _I, _I, _I, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fd_weights": (_I, [_P, _I, _P, _P, _P, _P]),
     "fd_cfl_limit": (_I, [_P, _P]),
     "fd_ricker": (_I, [_D, _D, _I, _P]),
@@ -310,6 +311,33 @@ def fd_dft_gamma(num, ref, nfreq: int = 0, with_gamma: bool = True, stream=None)
                               _addr(g) if g is not None else None, _addr(norms), _addr(agg),
                               _stream_ptr(stream)))
     return g, norms, agg, (sn, sr)
+
+
+def fd_cwt_gamma(num, ref, nscale: int = 0, omega0: float = 6.0, with_gamma: bool = True,
+                 stream=None):
+    """Wavelet (CWT) dispersion metric of Appendix A for traces num, ref
+    [nt, nrec] (float32 device tensors).  Returns (gamma [nrec, nscale, nt]
+    float32 or None, trace norms [nrec] float64, (average, maximum) float64
+    [2], largest |S^num| per trace [nrec] float64, and the two transforms
+    [nrec, nscale, nt, 2] float64); nscale defaults to nt // 2 + 1."""
+    import torch
+    nt, nrec = num.shape
+    assert ref.shape == num.shape and num.dtype == torch.float32 and ref.dtype == torch.float32
+    nscale = nscale or nt // 2 + 1
+    dev = num.device
+    spn = torch.empty((nrec, nt // 2 + 1, 2), dtype=torch.float64, device=dev)
+    spr = torch.empty_like(spn)
+    sn = torch.empty((nrec, nscale, nt, 2), dtype=torch.float64, device=dev)
+    sr = torch.empty_like(sn)
+    g = torch.empty((nrec, nscale, nt), dtype=torch.float32, device=dev) if with_gamma else None
+    amax = torch.empty(nrec, dtype=torch.float64, device=dev)
+    norms = torch.empty(nrec, dtype=torch.float64, device=dev)
+    agg = torch.empty(2, dtype=torch.float64, device=dev)
+    _check(lib().fd_cwt_gamma(_addr(num), _addr(ref), nt, nrec, nscale, omega0, _addr(spn),
+                              _addr(spr), _addr(sn), _addr(sr),
+                              _addr(g) if g is not None else None, _addr(amax), _addr(norms),
+                              _addr(agg), _stream_ptr(stream)))
+    return g, norms, agg, amax, (sn, sr)
 
 
 def fd_adjoint_gradient(plan: Plan, model, src_idx, wavelet, rec_idx, resid, k: int, grad, ws,
