@@ -160,7 +160,9 @@ def run_gpu(args):
             rec_idx = plan.linear_index(pr.rec)
         wav = torch.from_numpy(F.fd_ricker(pr.f0, dt, nt)[:, None].copy()).to(dev)
         tr = torch.empty((nt, len(rec_idx)), device=dev)
-        ws = F.workspace(plan.forward_workspace_size(1, len(rec_idx)), dev)
+        # the nt = 0 plan keeps the default tile shape: size for both plans
+        ws = F.workspace(max(plan.forward_workspace_size(1, len(rec_idx)),
+                             plan0.forward_workspace_size(1, len(rec_idx))), dev)
         runs.append(dict(name="%s%d_%s" % (shape, M, scheme), plan=plan, plan0=plan0, wav=wav,
                          tr=tr, ws=ws, dt=dt, tile=tile))
     inf = runs[0]["plan"].info()
@@ -317,7 +319,8 @@ def run_other(args):
             si, ri = plan.linear_index(pr.src), plan.linear_index(pr.rec)
             wav = torch.from_numpy(F.fd_ricker(pr.f0, pw_dt, pr.nt)[:, None].copy()).to(dev)
             tr = torch.empty((pr.nt, len(ri)), device=dev)
-            ws = F.workspace(plan.forward_workspace_size(1, len(ri)), dev)
+            ws = F.workspace(max(plan.forward_workspace_size(1, len(ri)),
+                                 plan0.forward_workspace_size(1, len(ri))), dev)
             inf = plan.info()
             pts = int(inf.padded[0] * inf.padded[2])
 
