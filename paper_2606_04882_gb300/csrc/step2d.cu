@@ -915,8 +915,11 @@ KernelFn lookup_fast(int shape, int M, int R, int mode)
 #define FDW_C(S, MM, RR) \
     if (shape == S && M == MM && R == RR) return pick_mode<S, MM, RR>(mode);
     FDW_C(FD_CROSS, 2, 1) FDW_C(FD_CROSS, 4, 1) FDW_C(FD_CROSS, 8, 1)
+    FDW_C(FD_CROSS, 2, 2) FDW_C(FD_CROSS, 4, 2) FDW_C(FD_CROSS, 8, 2)
     FDW_C(FD_CROSS, 2, 4) FDW_C(FD_CROSS, 4, 4) FDW_C(FD_CROSS, 8, 4)
+    FDW_C(FD_RHOMBUS, 2, 2) FDW_C(FD_RHOMBUS, 4, 2) FDW_C(FD_RHOMBUS, 8, 2)
     FDW_C(FD_RHOMBUS, 2, 4) FDW_C(FD_RHOMBUS, 4, 4) FDW_C(FD_RHOMBUS, 8, 4)
+    FDW_C(FD_SQUARE, 2, 2) FDW_C(FD_SQUARE, 4, 2) FDW_C(FD_SQUARE, 8, 2)
     FDW_C(FD_SQUARE, 2, 4) FDW_C(FD_SQUARE, 4, 4) FDW_C(FD_SQUARE, 8, 4)
 #undef FDW_C
     return nullptr;
@@ -940,8 +943,11 @@ PersistFn lookup_persist(int shape, int M, int R)
 #define FDW_P(S, MM, RR) \
     if (shape == S && M == MM && R == RR) return step2d_persistent<S, MM, RR>;
     FDW_P(FD_CROSS, 2, 1) FDW_P(FD_CROSS, 4, 1) FDW_P(FD_CROSS, 8, 1)
+    FDW_P(FD_CROSS, 2, 2) FDW_P(FD_CROSS, 4, 2) FDW_P(FD_CROSS, 8, 2)
     FDW_P(FD_CROSS, 2, 4) FDW_P(FD_CROSS, 4, 4) FDW_P(FD_CROSS, 8, 4)
+    FDW_P(FD_RHOMBUS, 2, 2) FDW_P(FD_RHOMBUS, 4, 2) FDW_P(FD_RHOMBUS, 8, 2)
     FDW_P(FD_RHOMBUS, 2, 4) FDW_P(FD_RHOMBUS, 4, 4) FDW_P(FD_RHOMBUS, 8, 4)
+    FDW_P(FD_SQUARE, 2, 2) FDW_P(FD_SQUARE, 4, 2) FDW_P(FD_SQUARE, 8, 2)
     FDW_P(FD_SQUARE, 2, 4) FDW_P(FD_SQUARE, 4, 4) FDW_P(FD_SQUARE, 8, 4)
 #undef FDW_P
     return nullptr;
@@ -1071,7 +1077,7 @@ cudaError_t launch_batched2d2(const Variant &v, const BatchParams &bp, int ntile
 int variants_2d(int shape, int M, int *r_out, int cap)
 {
     int n = 0;
-    for (int r : {4, 1})
+    for (int r : {4, 2, 1})
         if (n < cap && lookup_fast(shape, M, r, 0)) r_out[n++] = r;
     return n;
 }
@@ -1084,12 +1090,18 @@ int select_variant_2d(int shape, int M, int N, int64_t nx, int64_t nz, Variant *
     v->N = N;
     v->threads = kThreads;
     v->tx = kTX;
-    // R = 4 rows per thread when the grid has enough tiles to fill the GPU
-    // (two CTAs per SM on 152 SMs), else one row per thread.
-    const int64_t tiles4 = ((nx + kTX - 1) / kTX) * ((nz + 4 * kTZ - 1) / (4 * kTZ));
-    int R = r_pref > 0 ? r_pref : (tiles4 >= 2 * 152 ? 4 : 1);
-    if (!lookup_fast(shape, M, R, 0)) R = 5 - R;
-    v->generic = lookup_fast(shape, M, R, 0) ? 0 : 1;
+    // R rows per thread: the preferred R when it is compiled, else the largest
+    // compiled R whose tiles still fill the GPU (two CTAs per SM on 152 SMs),
+    // else the smallest compiled R; the generic kernel runs R = 1.
+    auto tiles = [&](int r) {
+        return ((nx + kTX - 1) / kTX) * ((nz + r * kTZ - 1) / (r * kTZ));
+    };
+    int R = r_pref > 0 && lookup_fast(shape, M, r_pref, 0) ? r_pref : 0;
+    for (int r : {4, 2, 1})
+        if (!R && lookup_fast(shape, M, r, 0) && tiles(r) >= 2 * 152) R = r;
+    for (int r : {1, 2, 4})
+        if (!R && lookup_fast(shape, M, r, 0)) R = r;
+    v->generic = R ? 0 : 1;
     if (v->generic) R = 1;
     v->tz = kTZ * R;
     const int HX = round4(M);
