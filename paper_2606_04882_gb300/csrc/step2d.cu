@@ -45,14 +45,6 @@ __device__ __forceinline__ void for_row(const PtEntry *tab, int b, int e, int zg
     }
 }
 
-// The same over a tile's whole range in a CSR table (ptr[tile] .. ptr[tile+1]).
-template <class F>
-__device__ __forceinline__ void for_owned(const int32_t *ptr, const PtEntry *tab, int tile, int zg,
-                                          int tx, F f)
-{
-    for_row(tab, ptr[tile], ptr[tile + 1], zg, tx, f);
-}
-
 // Laplacian sum of 4 consecutive columns col0 .. col0+3 of shared-memory row zl
 // (row width SW floats, at least round4(M) columns of halo on either side of
 // them, col0 a multiple of 4); cc receives the centre values.
@@ -177,6 +169,10 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
     float d2x[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) d2x[j] = layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]);
+    // the tile's ranges in the point tables, read once while the copy is in
+    // flight; most tiles have empty ranges and touch the tables no further
+    const int ib = p.inj_ptr ? p.inj_ptr[tile] : 0, ie = p.inj_ptr ? p.inj_ptr[tile + 1] : 0;
+    const int sb = p.smp_ptr ? p.smp_ptr[tile] : 0, se = p.smp_ptr ? p.smp_ptr[tile + 1] : 0;
 
     const bool ok = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!ok)) {
@@ -203,8 +199,8 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
             dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
         }
         // injection inside the bracket; adjoint residuals are scaled by kappa
-        if (p.inj_ptr)
-            for_owned(p.inj_ptr, p.inj, tile, z0 + ty * R + r, tx, [&](int j, const PtEntry &en) {
+        if (ib < ie)
+            for_row(p.inj, ib, ie, zg, tx, [&](int j, const PtEntry &en) {
                 float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
                 if (MODE == kModeAdjoint) a *= kk[j];
 #pragma unroll
@@ -214,8 +210,8 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
-        if (p.smp_ptr)
-            for_owned(p.smp_ptr, p.smp, tile, z0 + ty * R + r, tx, [&](int j, const PtEntry &en) {
+        if (sb < se)
+            for_row(p.smp, sb, se, zg, tx, [&](int j, const PtEntry &en) {
                 float v = 0.f;
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
@@ -827,6 +823,8 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
         mbar_arrive_expect_tx(&bar, SW * SH * 4);
         tma_load_2d(sm, p.tmap, &bar, x0 - HX, z0 - M);
     }
+    const int ib = p.inj_ptr ? p.inj_ptr[tile] : 0, ie = p.inj_ptr ? p.inj_ptr[tile + 1] : 0;
+    const int sb = p.smp_ptr ? p.smp_ptr[tile] : 0, se = p.smp_ptr ? p.smp_ptr[tile + 1] : 0;
     const bool ok = mbar_wait_bounded(&bar, 0);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
@@ -868,8 +866,8 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
         dv[j] = step_update(c, uu[j], kk[j], lap, gm[j], o[j]);
     }
     float4 br = make_float4(o[0], o[1], o[2], o[3]);
-    if (p.inj_ptr)
-        for_owned(p.inj_ptr, p.inj, tile, z0 + ty, tx, [&](int j, const PtEntry &en) {
+    if (ib < ie)
+        for_row(p.inj, ib, ie, zg, tx, [&](int j, const PtEntry &en) {
             float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
             if (MODE == kModeAdjoint) a *= kk[j];
             add4(br, j, a);
@@ -878,8 +876,8 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
     for (int j = 0; j < 4; ++j)
         if (gm[j] != 0.f) o[j] = __fdividef(o[j], 1.f + gm[j]);
     const float4 un = make_float4(o[0], o[1], o[2], o[3]);
-    if (p.smp_ptr)
-        for_owned(p.smp_ptr, p.smp, tile, z0 + ty, tx, [&](int j, const PtEntry &en) {
+    if (sb < se)
+        for_row(p.smp, sb, se, zg, tx, [&](int j, const PtEntry &en) {
             float v = get4(un, j) * en.scale;
             if (MODE == kModeAdjoint) v /= kk[j];
             p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
