@@ -28,6 +28,7 @@ struct fd_plan {
     int64_t pitch = 0, plane = 0, field = 0;   // floats
     fdw::Variant var{};
     int tiles_x = 0, tiles_y = 0, ntiles = 0;
+    int max_tiles = 0;   // largest tile count of any variant the plan can take
     int zchunk = 0, nz_chunks = 1;
     bool tuned = false;
     float gcoef = 0.f;
@@ -102,9 +103,12 @@ size_t table_bytes_n(int ntiles, int nsrc, int nrec, bool adj)
     return adj ? 2 * b : b;
 }
 
+// Point tables are sized for the plan's largest tile count, so that one
+// workspace size serves every kernel variant (the default, each autotune
+// candidate and the tuned choice).
 size_t table_bytes(const fd_plan *p, int nsrc, int nrec, bool adj)
 {
-    return table_bytes_n(p->ntiles, nsrc, nrec, adj);
+    return table_bytes_n(std::max(p->ntiles, p->max_tiles), nsrc, nrec, adj);
 }
 
 Layout make_layout(const fd_plan *p, int nsrc, int nrec, bool grad, int kseg, int ntiles_tab = -1)
@@ -435,6 +439,21 @@ extern "C" int fd_plan_create(const fd_problem *prob, const fd_stencil_desc *ste
         return set_error(FD_ERR_UNSUPPORTED, "no kernel for shape %d, M %d in %dD", p->shape_eff, M, pr.dim);
     }
     p->ntiles = p->tiles_x * p->tiles_y;
+    p->max_tiles = p->ntiles;
+    {
+        int prefs[4];
+        const int np = pr.dim == 2 ? variants_2d(p->shape_eff, M, prefs, 4)
+                                   : variants_3d(p->shape_eff, M, prefs, 4);
+        for (int i = 0; i < np; ++i) {
+            Variant v;
+            if (pr.dim == 2 ? select_variant_2d(p->shape_eff, M, stencil->N, padx, padz, &v, prefs[i])
+                            : select_variant_3d(p->shape_eff, M, stencil->N, padx, pady, padz, &v, prefs[i]))
+                continue;
+            const int64_t n = ((padx + v.tx - 1) / v.tx) *
+                              (((pr.dim == 2 ? padz : pady) + v.tz - 1) / v.tz);
+            p->max_tiles = (int)std::max<int64_t>(p->max_tiles, n);
+        }
+    }
     if (pr.nb > 0) {
         const double R = pr.damp_R > 0 ? pr.damp_R : 1e-3;
         const double eta_max = 3.0 * pr.vmax * std::log(1.0 / R) / (2.0 * pr.nb * pr.h);
