@@ -25,6 +25,11 @@ def shard(nshots: int, rank: int, world: int) -> List[int]:
     return list(range(lo, hi))
 
 
+class RankFailure(RuntimeError):
+    """Another rank failed its shots: raised on the ranks that did not, in
+    place of the reduction (which would mix in a partial gradient)."""
+
+
 def _dist():
     try:
         import torch.distributed as dist
@@ -41,22 +46,41 @@ def misfit_and_gradient(template, nshots: int,
     """Sum (J_s, g_s) over this rank's shots, then all-reduce the sums over
     ranks.  ``per_shot(s)`` returns (J_s, g_s) with g_s a tensor shaped like
     `template` (which fixes shape, dtype and device, so that ranks without
-    shots contribute zeros).  Returns (J, g), identical on every rank."""
+    shots contribute zeros).  Returns (J, g), identical on every rank.
+
+    Failures: the ranks first all-reduce a count of failed ranks.  A rank
+    whose shots raised re-raises its exception after that exchange, and the
+    others raise RankFailure, so no rank waits in the reduction for a rank
+    that has given up.  A rank that never reaches the exchange (it died or
+    hangs) is caught by the process group's timeout, which ends the
+    collective with an error on the others."""
     import torch
     dist = _dist()
     if rank is None or world is None:
         rank, world = (dist.get_rank(), dist.get_world_size()) if dist else (0, 1)
     g = torch.zeros_like(template)
     J = 0.0
-    for s in shard(nshots, rank, world):
-        Js, gs = per_shot(s)
-        J += float(Js)
-        g.add_(gs)
+    err = None
+    try:
+        for s in shard(nshots, rank, world):
+            Js, gs = per_shot(s)
+            J += float(Js)
+            g.add_(gs)
+    except Exception as e:        # reported to the other ranks below
+        err = e
     if dist is not None and world > 1:
+        failed = torch.tensor([0.0 if err is None else 1.0], dtype=torch.float64, device=g.device)
+        dist.all_reduce(failed)
+        if err is not None:
+            raise err
+        if failed.item() > 0:
+            raise RankFailure("%d of %d ranks failed their shots" % (int(failed.item()), world))
         Jt = torch.tensor([J], dtype=g.dtype, device=g.device)
         dist.all_reduce(Jt)
         dist.all_reduce(g)
         J = float(Jt.item())
+    elif err is not None:
+        raise err
     return J, g
 
 

@@ -83,3 +83,54 @@ def test_gloo_ranks_reduce_to_the_single_process_sum(world, nshots):
         J, g = out[r]
         assert abs(J - J0) <= 1e-12 * abs(J0)
         assert np.allclose(g, g0, rtol=1e-12, atol=1e-12 * np.abs(g0).max())
+
+
+def _failing_rank_main(rank, world, port, mode, out):
+    """mode 'raise': rank 1's shot raises; mode 'absent': rank 1 never joins
+    the reduction (it leaves between steps)."""
+    import datetime
+    import time
+    from paper_2606_04882_gb300.shots import RankFailure
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+
+    def per_shot(s):
+        if rank == 1 and mode == "raise":
+            raise ValueError("shot %d failed" % s)
+        return 1.0, torch.ones(4, dtype=torch.float64)
+
+    t0 = time.time()
+    if rank == 1 and mode == "absent":
+        time.sleep(8)             # past the others' collective timeout
+        out[rank] = ("left", 0.0)
+        return
+    try:
+        misfit_and_gradient(torch.zeros(4, dtype=torch.float64), 4, per_shot)
+        out[rank] = ("ok", time.time() - t0)
+    except RankFailure:
+        out[rank] = ("rank_failure", time.time() - t0)
+    except ValueError:
+        out[rank] = ("own_error", time.time() - t0)
+    except RuntimeError:
+        out[rank] = ("collective_error", time.time() - t0)
+    dist.destroy_process_group()
+
+
+def test_a_failing_rank_is_reported_to_the_others():
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_failing_rank_main, args=(2, _free_port(), "raise", out), nprocs=2,
+                       join=True, start_method="spawn")
+    assert out[1][0] == "own_error"
+    assert out[0][0] == "rank_failure" and out[0][1] < 5.0
+
+
+def test_an_absent_rank_ends_the_collective_by_timeout():
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_failing_rank_main, args=(2, _free_port(), "absent", out), nprocs=2,
+                       join=True, start_method="spawn")
+    assert out[1][0] == "left"
+    assert out[0][0] == "collective_error" and out[0][1] < 8.0
