@@ -191,7 +191,9 @@ int fd_plan_autotune(fd_plan *plan, int model_kind, const float *model_d, void *
 /*
  * fd_forward_workspace_size - bytes of device workspace fd_forward needs for
  * nsrc sources and nrec receivers (three padded field buffers, tile-bucketed
- * source/receiver tables, the status word).
+ * source/receiver tables, the status word).  The tables are sized for the
+ * plan's largest tile count, so the size does not depend on the kernel
+ * variant fd_plan_autotune chooses.
  */
 int fd_forward_workspace_size(const fd_plan *plan, int nsrc, int nrec, size_t *bytes);
 
