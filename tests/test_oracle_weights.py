@@ -300,3 +300,52 @@ def test_cfl_closed_form_and_brute_force():
     g = np.linspace(0, np.pi, 301)
     K = np.array(np.meshgrid(g, g, indexing="ij")).reshape(2, -1).T
     assert np.max(-S.symbol(pw, K)) <= 4 / cm ** 2 * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("scheme,C", [("displs", 0.3), ("displs", 0.6), ("specls", 0.0)])
+def test_ls_single_unknown_has_the_closed_form_minimiser(scheme, C):
+    """Cross(1) in 2D has one least-squares unknown a (the axis weight), so
+    the minimiser of the functional over beta in [0, b], theta in [0, 2 pi]
+    (Eqs. cont_dotprod, LS_disp_error, cosine basis) is a = <Phi, 1> / <Phi, Phi>
+    with Phi = (4 - 2 cos(beta cos theta) - 2 cos(beta sin theta)) / Psi(beta),
+    Psi = (2 - 2 cos C beta)/C^2 (DispLS) or beta^2 (SpecLS).  Evaluated here
+    by adaptive quadrature in half-angle form, independent of the oracle's
+    Gauss-Legendre and trapezoid rules."""
+    integrate = pytest.importorskip("scipy.integrate")
+    b = np.pi / 2
+
+    def phi(th, beta):
+        num = 4 * np.sin(0.5 * beta * np.cos(th)) ** 2 + 4 * np.sin(0.5 * beta * np.sin(th)) ** 2
+        psi = (2 * np.sin(0.5 * C * beta) / C) ** 2 if C > 0 else beta ** 2
+        return num / psi
+
+    opts = dict(epsabs=1e-14, epsrel=1e-13)
+    p1 = integrate.dblquad(lambda th, beta: phi(th, beta), 0, b, 0, 2 * np.pi, **opts)[0]
+    p2 = integrate.dblquad(lambda th, beta: phi(th, beta) ** 2, 0, b, 0, 2 * np.pi, **opts)[0]
+    a = p1 / p2
+    w = S.weights(2, "cross", 1, 0, scheme, C=C, b=b, basis="cosine")
+    assert abs(w[(1, 0)] - a) < 1e-10 * abs(a)
+    assert abs(w[(0, 0)] + 4 * a) < 1e-10 * abs(a)
+
+
+def test_ls_single_unknown_closed_form_in_3d():
+    """The same for the 3D Cross(1) DispLS weight, with directions over the
+    unit sphere (mu = cos of the polar angle, azimuth phi):
+    Phi = (6 - 2 cos(beta kx) - 2 cos(beta ky) - 2 cos(beta kz)) / Psi(beta)."""
+    integrate = pytest.importorskip("scipy.integrate")
+    b, C = np.pi / 2, 0.4
+
+    def phi(ph, mu, beta):
+        st = np.sqrt(max(0.0, 1.0 - mu * mu))
+        k = (st * np.cos(ph), st * np.sin(ph), mu)
+        num = sum(4 * np.sin(0.5 * beta * kc) ** 2 for kc in k)
+        return num / (2 * np.sin(0.5 * C * beta) / C) ** 2
+
+    opts = dict(epsabs=1e-12, epsrel=1e-11)
+    p1 = integrate.tplquad(lambda ph, mu, beta: phi(ph, mu, beta), 0, b, -1, 1, 0, 2 * np.pi, **opts)[0]
+    p2 = integrate.tplquad(lambda ph, mu, beta: phi(ph, mu, beta) ** 2, 0, b, -1, 1, 0, 2 * np.pi,
+                           **opts)[0]
+    a = p1 / p2
+    w = S.weights(3, "cross", 1, 0, "displs", C=C, b=b, basis="cosine")
+    assert abs(w[(1, 0, 0)] - a) < 1e-8 * abs(a)
+    assert abs(w[(0, 0, 0)] + 6 * a) < 1e-8 * abs(a)
