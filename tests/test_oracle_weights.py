@@ -349,3 +349,37 @@ def test_ls_single_unknown_closed_form_in_3d():
     w = S.weights(3, "cross", 1, 0, "displs", C=C, b=b, basis="cosine")
     assert abs(w[(1, 0, 0)] - a) < 1e-8 * abs(a)
     assert abs(w[(0, 0, 0)] + 6 * a) < 1e-8 * abs(a)
+
+
+@pytest.mark.parametrize("shape,orbits", [
+    ("cross", {(1, 0): [(1, 0), (-1, 0), (0, 1), (0, -1)],
+               (2, 0): [(2, 0), (-2, 0), (0, 2), (0, -2)]}),
+    ("rhombus", {(1, 0): [(1, 0), (-1, 0), (0, 1), (0, -1)],
+                 (2, 0): [(2, 0), (-2, 0), (0, 2), (0, -2)],
+                 (1, 1): [(1, 1), (1, -1), (-1, 1), (-1, -1)]}),
+])
+def test_ls_normal_equations_by_adaptive_quadrature(shape, orbits):
+    """DispLS for radius 2 (two and three unknowns): the weights solve the
+    normal equations <Phi_i, Phi_j> a_j = <Phi_i, 1> of the paper's functional
+    (cosine basis, Eq. displs_cont_linsys), with every inner product taken by
+    adaptive quadrature from orbit point lists written out here."""
+    integrate = pytest.importorskip("scipy.integrate")
+    b, C = np.pi / 2, 0.3
+    keys = list(orbits)
+
+    def phi(key, th, beta):
+        kz, kx = np.sin(th), np.cos(th)
+        num = sum(4 * np.sin(0.5 * beta * (kz * o[0] + kx * o[1])) ** 2 / 2 for o in orbits[key])
+        return num / (2 * np.sin(0.5 * C * beta) / C) ** 2
+
+    def ip(f):
+        return integrate.dblquad(lambda th, beta: f(th, beta), 0, b, 0, 2 * np.pi,
+                                 epsabs=1e-13, epsrel=1e-12)[0]
+
+    G = np.array([[ip(lambda th, be, i=i, j=j: phi(i, th, be) * phi(j, th, be)) for j in keys]
+                  for i in keys])
+    r = np.array([ip(lambda th, be, i=i: phi(i, th, be)) for i in keys])
+    a = np.linalg.solve(G, r)
+    w = S.weights(2, shape, 2, 0, "displs", C=C, b=b, basis="cosine")
+    for k, v in zip(keys, a):
+        assert abs(w[k] - v) < 1e-8 * np.abs(a).max(), (k, w[k], v)
