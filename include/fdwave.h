@@ -116,9 +116,14 @@ int fd_weights(const fd_stencil_desc *desc, int cap, int *n_orbits,
 
 /*
  * fd_cfl_limit - von Neumann stability limit of the leapfrog with this
- * stencil: C_max = 2 / sqrt(max_k -S(k)), S(k) = sum_o a_o cos(k.o) (the
- * symbol in Eq. full_disp).  A run is stable when c_max tau / h <= C_max.
- * HOST, FP64.  Errors: as fd_weights.
+ * stencil, from the symbol S(k) = sum_o a_o cos(k.o) of Eq. full_disp.  The
+ * amplification equation lambda^2 - (2 + C^2 S(k)) lambda + 1 = 0 has both
+ * roots on the unit circle iff -4 <= C^2 S(k) <= 0 for every k, so:
+ *   - C_max = 2 / sqrt(max_k -S(k)); a run is stable when c_max tau / h <= C_max;
+ *   - a stencil whose symbol is positive somewhere (above 1e-9 max(-S), far
+ *     beyond the round-off of S(0) = 0) is unstable at every time step and
+ *     gets FD_ERR_UNSTABLE (fd_last_error names the wave number).
+ * HOST, FP64.  Errors: as fd_weights, and FD_ERR_UNSTABLE.
  */
 int fd_cfl_limit(const fd_stencil_desc *desc, double *courant_max);
 
@@ -152,8 +157,9 @@ typedef enum { FD_MODEL_VELOCITY = 0, FD_MODEL_SLOWNESS2 = 1 } fd_model_kind;
 
 /*
  * fd_plan_create - validate a problem and stencil, solve the weights (host
- * FP64, rounded to FP32 for the kernels), check vmax dt / h <= C_max
- * (FD_ERR_UNSTABLE otherwise) and choose the kernel variant.  The plan owns
+ * FP64, rounded to FP32 for the kernels), check vmax dt / h <= C_max of
+ * fd_cfl_limit (FD_ERR_UNSTABLE otherwise, and for a stencil that no time
+ * step makes stable) and choose the kernel variant.  The plan owns
  * only host memory.  Errors: FD_ERR_ARG, FD_ERR_UNSTABLE, FD_ERR_SINGULAR,
  * FD_ERR_UNSUPPORTED, FD_ERR_NOMEM.
  */

@@ -399,32 +399,58 @@ def omega_fd(pts_w, k: np.ndarray, C: float, tau: float) -> np.ndarray:
     return np.arccos(1.0 + 0.5 * C * C * symbol(pts_w, k)) / tau
 
 
-def cfl_limit(pts_w, dim: int, n_grid: int = 129) -> float:
-    """Von Neumann bound of the leapfrog scheme: with lambda^2 - (2 + C^2 S)
-    lambda + 1 = 0 the roots stay on the unit circle iff C^2 max(-S) <= 4, so
-    C_max = 2 / sqrt(max_k -S(k)) over k in [0, pi]^dim.  Brute force on a
-    regular grid (which contains every corner), refined by a local search."""
+SYMBOL_POSITIVE_TOL = 1e-9
+
+
+def _extreme_symbol(pts_w, dim: int, sign: float, n_grid: int):
+    """max_k sign * S(k) over k in [0, pi]^dim: brute force on a regular grid
+    (which contains every corner), refined by a bounded local search."""
     g = np.linspace(0.0, np.pi, n_grid)
     best, kbest = -np.inf, None
-    if dim == 2:
-        K = np.array(np.meshgrid(g, g, indexing="ij")).reshape(2, -1).T
-        s = -symbol(pts_w, K)
-        i = int(np.argmax(s))
-        best, kbest = s[i], K[i]
-    else:
-        for a in g:
+    slabs = [None] if dim == 2 else list(g)
+    for a in slabs:
+        if dim == 2:
+            K = np.array(np.meshgrid(g, g, indexing="ij")).reshape(2, -1).T
+        else:
             K = np.array(np.meshgrid([a], g, g, indexing="ij")).reshape(3, -1).T
-            s = -symbol(pts_w, K)
-            i = int(np.argmax(s))
-            if s[i] > best:
-                best, kbest = s[i], K[i]
+        s = sign * symbol(pts_w, K)
+        i = int(np.argmax(s))
+        if s[i] > best:
+            best, kbest = float(s[i]), K[i]
     try:
         from scipy.optimize import minimize
-        res = minimize(lambda k: symbol(pts_w, np.clip(k, 0, np.pi))[0], kbest,
+        res = minimize(lambda k: -sign * symbol(pts_w, np.clip(k, 0, np.pi))[0], kbest,
                        method="L-BFGS-B", bounds=[(0, np.pi)] * dim)
-        best = max(best, -float(res.fun))
+        if -float(res.fun) > best:
+            best, kbest = -float(res.fun), np.clip(res.x, 0, np.pi)
     except Exception:  # pragma: no cover
         pass
-    if best <= 0:
+    return best, kbest
+
+
+def symbol_range(pts_w, dim: int, n_grid: int = 129):
+    """(min_k S(k), max_k S(k)) over k in [0, pi]^dim (the symbol is even and
+    2 pi-periodic in every component, so this is its range on all of R^dim)."""
+    neg, _ = _extreme_symbol(pts_w, dim, -1.0, n_grid)
+    pos, _ = _extreme_symbol(pts_w, dim, +1.0, n_grid)
+    return -neg, pos
+
+
+def cfl_limit(pts_w, dim: int, n_grid: int = 129) -> float:
+    """Von Neumann bound of the leapfrog scheme (Eq. full_disp written as the
+    amplification equation lambda^2 - (2 + C^2 S) lambda + 1 = 0): the product
+    of the two roots is 1, so both stay on the unit circle iff their sum
+    2 + C^2 S(k) lies in [-2, 2], i.e. iff -4 <= C^2 S(k) <= 0 for every k.
+
+    - If S(k) > 0 anywhere, one root is real and larger than 1 for every
+      C > 0: no time step is stable and a ValueError is raised.  S(0) = 0 for a
+      consistent stencil, so "positive" means above SYMBOL_POSITIVE_TOL times
+      max(-S), far above the round-off of S(0) and far below a real violation.
+    - Otherwise C_max = 2 / sqrt(max_k -S(k))."""
+    smin, smax = symbol_range(pts_w, dim, n_grid)
+    if -smin <= 0:
         raise ValueError("stencil symbol is non-negative: no stable time step")
-    return 2.0 / math.sqrt(best)
+    if smax > SYMBOL_POSITIVE_TOL * (-smin):
+        raise ValueError("stencil symbol reaches %.6g > 0: the leapfrog is unstable "
+                         "at every time step" % smax)
+    return 2.0 / math.sqrt(-smin)

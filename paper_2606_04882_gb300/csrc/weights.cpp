@@ -580,15 +580,52 @@ int compute_weights(const fd_stencil_desc *d, std::vector<std::array<int, 3>> &k
     return FD_OK;
 }
 
-double symbol_neg(const std::vector<std::array<int, 3>> &offs, const std::vector<double> &wo,
-                  const double k[3])
+double symbol_at(const std::vector<std::array<int, 3>> &offs, const std::vector<double> &wo,
+                 const double k[3])
 {
     double s = 0.0;
     for (size_t i = 0; i < offs.size(); ++i)
         s += wo[i] * std::cos(k[0] * offs[i][0] + k[1] * offs[i][1] + k[2] * offs[i][2]);
-    return -s;
+    return s;
 }
 
+// max over k in [0, pi]^dim of sign * S(k): a regular grid (corners included),
+// then a compass pattern search from the best grid point.
+static double symbol_extreme(const std::vector<std::array<int, 3>> &offs,
+                             const std::vector<double> &wo, int dim, double sign, double kb[3])
+{
+    const int G = dim == 2 ? 97 : 33;
+    double best = -1e300;
+    kb[0] = kb[1] = kb[2] = 0.0;
+    for (int a = 0; a < G; ++a)
+        for (int bb = 0; bb < (dim == 3 ? G : 1); ++bb)
+            for (int c = 0; c < G; ++c) {
+                double k[3] = {kPi * a / (G - 1), dim == 3 ? kPi * bb / (G - 1) : 0.0, kPi * c / (G - 1)};
+                const double v = sign * symbol_at(offs, wo, k);
+                if (v > best) { best = v; std::memcpy(kb, k, 3 * sizeof(double)); }
+            }
+    double h = kPi / (G - 1);
+    while (h > 1e-12) {
+        bool moved = false;
+        for (int ax = 0; ax < 3; ++ax) {
+            if (dim == 2 && ax == 1) continue;
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                double k[3] = {kb[0], kb[1], kb[2]};
+                k[ax] = std::min(kPi, std::max(0.0, k[ax] + sgn * h));
+                const double v = sign * symbol_at(offs, wo, k);
+                if (v > best) { best = v; std::memcpy(kb, k, 3 * sizeof(double)); moved = true; }
+            }
+        }
+        if (!moved) h *= 0.5;
+    }
+    return best;
+}
+
+// Von Neumann bound of the leapfrog (Eq. full_disp as the amplification
+// equation lambda^2 - (2 + C^2 S) lambda + 1 = 0, whose roots have product 1):
+// both roots lie on the unit circle iff -4 <= C^2 S(k) <= 0 for every k.  A
+// symbol that is positive anywhere (beyond round-off: kSymbolPositiveTol of
+// max -S; S(0) = 0 for a consistent stencil) is unstable at every time step.
 int compute_cfl(const fd_stencil_desc *d, const std::vector<double> &w, double *cmax)
 {
     std::vector<std::array<int, 3>> keys, offs;
@@ -599,32 +636,16 @@ int compute_cfl(const fd_stencil_desc *d, const std::vector<double> &w, double *
     std::vector<double> wo(offs.size());
     for (size_t i = 0; i < offs.size(); ++i) wo[i] = w[oo[i]];
     const int dim = d->dim;
-    const int G = dim == 2 ? 97 : 33;
-    double best = -1e300, kb[3] = {0, 0, 0};
-    for (int a = 0; a < G; ++a)
-        for (int bb = 0; bb < (dim == 3 ? G : 1); ++bb)
-            for (int c = 0; c < G; ++c) {
-                double k[3] = {kPi * a / (G - 1), dim == 3 ? kPi * bb / (G - 1) : 0.0, kPi * c / (G - 1)};
-                const double v = symbol_neg(offs, wo, k);
-                if (v > best) { best = v; std::memcpy(kb, k, sizeof kb); }
-            }
-    // pattern search refinement inside [0, pi]^dim
-    double h = kPi / (G - 1);
-    while (h > 1e-12) {
-        bool moved = false;
-        for (int ax = 0; ax < 3; ++ax) {
-            if (dim == 2 && ax == 1) continue;
-            for (int sgn = -1; sgn <= 1; sgn += 2) {
-                double k[3] = {kb[0], kb[1], kb[2]};
-                k[ax] = std::min(kPi, std::max(0.0, k[ax] + sgn * h));
-                const double v = symbol_neg(offs, wo, k);
-                if (v > best) { best = v; std::memcpy(kb, k, sizeof kb); moved = true; }
-            }
-        }
-        if (!moved) h *= 0.5;
-    }
-    if (!(best > 0.0)) return set_error(FD_ERR_UNSTABLE, "stencil symbol is non-negative: no stable time step");
-    *cmax = 2.0 / std::sqrt(best);
+    constexpr double kSymbolPositiveTol = 1e-9;
+    double kneg[3], kpos[3];
+    const double neg = symbol_extreme(offs, wo, dim, -1.0, kneg);   // max -S
+    const double pos = symbol_extreme(offs, wo, dim, +1.0, kpos);   // max S
+    if (!(neg > 0.0)) return set_error(FD_ERR_UNSTABLE, "stencil symbol is non-negative: no stable time step");
+    if (pos > kSymbolPositiveTol * neg)
+        return set_error(FD_ERR_UNSTABLE,
+                         "stencil symbol S(k) = %.6g > 0 at k h = (%.4f, %.4f, %.4f): the leapfrog is "
+                         "unstable at every time step", pos, kpos[0], kpos[1], kpos[2]);
+    *cmax = 2.0 / std::sqrt(neg);
     return FD_OK;
 }
 

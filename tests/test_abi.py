@@ -64,8 +64,15 @@ def test_weights_and_cfl_match_oracle(dim, shape, M, N, scheme):
         kk = tuple(int(x) for x in k[:dim])
         assert mult[i] == len(orbs[kk])
         assert abs(w[i] - ow[kk]) <= tol * scale, (kk, w[i], ow[kk])
+    try:
+        oc = S.cfl_limit(S.expand(dim, shape, M, N, ow), dim)
+    except ValueError:
+        # the symbol is positive somewhere: both sides must refuse every dt
+        with pytest.raises(F.FdError) as e:
+            F.fd_cfl_limit(d)
+        assert e.value.code == F.FD_ERR_UNSTABLE
+        return
     c = F.fd_cfl_limit(d)
-    oc = S.cfl_limit(S.expand(dim, shape, M, N, ow), dim)
     assert abs(c - oc) < 1e-7 * oc
 
 
@@ -111,8 +118,11 @@ def test_plan_validation_and_stability_check():
         F.fd_weights(F.stencil_desc(3, "cross", 4, 0, "specte_theta"))
     assert e.value.code == F.FD_ERR_UNSUPPORTED
     with pytest.raises(F.FdError) as e:   # 3D cross-square kernels are not provided
-        F.Plan((20, 20, 20), h, 1e-4, 5, 2, v, F.stencil_desc(3, "cross_square", 4, 2, "dispte", courant=0.1))
+        F.Plan((20, 20, 20), h, 1e-4, 5, 2, v, F.stencil_desc(3, "cross_square", 4, 2, "displs", courant=0.1))
     assert e.value.code == F.FD_ERR_UNSUPPORTED
+    with pytest.raises(F.FdError) as e:   # its DispTE weights have S(k) > 0: no stable dt
+        F.Plan((20, 20, 20), h, 1e-4, 5, 2, v, F.stencil_desc(3, "cross_square", 4, 2, "dispte", courant=0.1))
+    assert e.value.code == F.FD_ERR_UNSTABLE
 
 
 def test_taylor_rhombus_reduces_to_cross_kernel():
@@ -135,3 +145,22 @@ def test_workspace_sizes():
     # gradient: 4 buffers + kappa + gacc + 2*10 checkpoints + 10 segment fields
     assert g >= (6 + 20 + 10) * field
     assert p.gradient_workspace_size(1, 100, 5) > g
+
+
+@pytest.mark.parametrize("M,N", [(2, 1), (4, 2), (6, 3)])
+def test_symbol_positive_stencil_is_rejected(M, N):
+    """A stencil whose symbol is positive somewhere (DispTE-CrossSq at C = 0.3)
+    has no stable time step: fd_cfl_limit and fd_plan_create refuse it, at any
+    dt, while the Taylor cross of the same radius is still accepted."""
+    d = F.stencil_desc(2, "cross_square", M, N, "dispte", courant=0.3)
+    with pytest.raises(F.FdError) as e:
+        F.fd_cfl_limit(d)
+    assert e.value.code == F.FD_ERR_UNSTABLE
+    assert "unstable at every time step" in str(e.value)
+    h, v = 10.0, 3000.0
+    for dt in (1e-6, 0.3 * h / v):
+        with pytest.raises(F.FdError) as e:
+            F.Plan((40, 40), h, dt, 10, 5, v, d)
+        assert e.value.code == F.FD_ERR_UNSTABLE
+    dc = F.stencil_desc(2, "cross", M)
+    F.Plan((40, 40), h, 0.5 * F.fd_cfl_limit(dc) * h / v, 10, 5, v, dc)

@@ -256,3 +256,27 @@ def test_pad_fold_adjoint():
         x = rng.standard_normal(shape)
         y = rng.standard_normal(tuple(s + 6 for s in shape))
         assert abs(np.sum(P.pad(x, 3) * y) - np.sum(x * P.fold(y, 3))) < 1e-10
+
+
+def test_symbol_positive_stencil_grows_at_the_predicted_rate():
+    """DispTE-CrossSq(2, 1) (weights at C = 0.3) run at a tenth of the Taylor
+    Cross(2) limit: its symbol peaks at S* > 0, so the largest root of
+    lambda^2 - (2 + C^2 S*) lambda + 1 = 0 exceeds 1 and a random field grows
+    by that factor per step (slightly less on a finite grid, whose modes only
+    approach the worst wave number)."""
+    w = S.weights(2, "cross_square", 2, 1, "dispte", C=0.3)
+    _, smax = S.symbol_range(S.expand(2, "cross_square", 2, 1, w), 2)
+    C = 0.1 * S.cfl_limit(S.expand(2, "cross", 2, 0, S.weights(2, "cross", 2)), 2)
+    n, v, h = 64, 1500.0, 10.0
+    st = W.Setup(np.full((n, n), v, dtype=np.float32), h, C * h / v, 0, v, 2,
+                 "cross_square", 2, 1, "dispte", weights=w)
+    u0 = np.random.default_rng(0).standard_normal((n, n))
+    amp = {}
+    for ns in (100, 150):
+        _, un, _ = W.forward(st, ns, None, None, None, u0=u0, um1=u0, threads=4)
+        amp[ns] = np.max(np.abs(un))
+    assert amp[100] > 1e6 * np.max(np.abs(u0))
+    x = 2.0 + C * C * smax
+    rate = math.log((x + math.sqrt(x * x - 4.0)) / 2.0)
+    measured = math.log(amp[150] / amp[100]) / 50
+    assert 0.9 * rate < measured <= 1.001 * rate, (measured, rate)

@@ -383,3 +383,49 @@ def test_ls_normal_equations_by_adaptive_quadrature(shape, orbits):
     w = S.weights(2, shape, 2, 0, "displs", C=C, b=b, basis="cosine")
     for k, v in zip(keys, a):
         assert abs(w[k] - v) < 1e-8 * np.abs(a).max(), (k, w[k], v)
+
+
+def _brute_force_symbol_max(pts, wo, n=241):
+    """max over a regular (kz, kx) grid of [0, pi]^2 of S(k) = sum_o w_o cos(k . o),
+    summed here offset by offset."""
+    g = np.linspace(0.0, np.pi, n)
+    best = -np.inf
+    for kz in g:
+        s = np.zeros_like(g)
+        for (dz, dx), wi in zip(pts, wo):
+            s += wi * np.cos(kz * dz + g * dx)
+        best = max(best, float(s.max()))
+    return best
+
+
+@pytest.mark.parametrize("M,N", [(2, 1), (4, 2), (6, 3)])
+def test_symbol_positive_stencil_has_no_stable_time_step(M, N):
+    """The leapfrog's amplification equation lambda^2 - (2 + C^2 S) lambda + 1 = 0
+    (Eq. full_disp) has a root above 1 wherever S(k) > 0, at every C > 0.
+    DispTE-CrossSq(M, N) at C = 0.3 has such wave numbers: the brute-force
+    maximum of its symbol is far above 0, and the bound must say that no time
+    step is stable instead of returning 2 / sqrt(max -S)."""
+    w = S.weights(2, "cross_square", M, N, "dispte", C=0.3)
+    pts = S.point_set(2, "cross_square", M, N)
+    wo = [w[tuple(sorted((abs(v) for v in o), reverse=True))] for o in pts]
+    smax = _brute_force_symbol_max(pts, wo)
+    assert smax > 1.0
+    pw = S.expand(2, "cross_square", M, N, w)
+    lo, hi = S.symbol_range(pw, 2)
+    assert smax - 1e-9 <= hi <= smax + 0.05 * smax
+    assert lo < 0
+    with pytest.raises(ValueError, match="unstable at every time step"):
+        S.cfl_limit(pw, 2)
+
+
+@pytest.mark.parametrize("dim,shape,M,N,scheme", [
+    (2, "cross", 4, 0, "spatte"), (2, "rhombus", 4, 0, "displs"), (2, "square", 4, 0, "displs"),
+    (2, "cross_square", 4, 2, "displs"), (3, "cross", 4, 0, "spatte"),
+])
+def test_stable_stencils_have_non_positive_symbol(dim, shape, M, N, scheme):
+    """Stencils the workloads run keep S(k) <= 0 up to round-off (S(0) = 0),
+    so the bound stays 2 / sqrt(max -S)."""
+    pw = S.expand(dim, shape, M, N, S.weights(dim, shape, M, N, scheme, C=0.3))
+    lo, hi = S.symbol_range(pw, dim, n_grid=65 if dim == 3 else 129)
+    assert hi <= 1e-12 * abs(lo)
+    assert abs(S.cfl_limit(pw, dim) - 2 / math.sqrt(-lo)) < 1e-12
