@@ -6,6 +6,7 @@ the paper's counting formulas, exact polynomial reproduction, the order of
 the dispersion error the scheme is defined by, the paper's special-case
 reductions, and an independent evaluation of the least-squares functional.
 """
+import itertools
 import math
 import os
 from fractions import Fraction
@@ -429,3 +430,105 @@ def test_stable_stencils_have_non_positive_symbol(dim, shape, M, N, scheme):
     lo, hi = S.symbol_range(pw, dim, n_grid=65 if dim == 3 else 129)
     assert hi <= 1e-12 * abs(lo)
     assert abs(S.cfl_limit(pw, dim) - 2 / math.sqrt(-lo)) < 1e-12
+
+
+def _orbit_offsets(key, dim):
+    """Every offset of a symmetry orbit: all permutations and sign changes of
+    its sorted absolute offsets (zero-padded to dim components)."""
+    full = tuple(key) + (0,) * (dim - len(key))
+    out = set()
+    for perm in itertools.permutations(full):
+        for sg in itertools.product((1, -1), repeat=dim):
+            out.add(tuple(s * v for s, v in zip(sg, perm)))
+    return sorted(out)
+
+
+def _displs_design(dim, keys, C, b, n_beta=24, n_dir=16):
+    """Design matrix of E_disp(b) (Eq. LS_disp_error, cosine basis of Eq.
+    displs_cont_linsys: Phi_orb = sum_{o in orb} (1 - cos(beta khat.o)) / Psi2,
+    Psi2 = (2 - 2 cos C beta) / C^2, target 1) on this test's own quadrature:
+    Gauss-Legendre in beta; in 2D the midpoint rule on one eighth of the
+    circle (the integrand has the square's eight-fold symmetry), in 3D
+    Gauss-Legendre in the polar angle (weight sin) and the midpoint rule in
+    azimuth.  Returns (A, quadrature weights)."""
+    xb, wb = np.polynomial.legendre.leggauss(n_beta)
+    beta, wbeta = 0.5 * b * (xb + 1), 0.5 * b * wb
+    if dim == 2:
+        th = (np.arange(n_dir) + 0.5) * (np.pi / 4) / n_dir
+        dirs = np.stack([np.sin(th), np.cos(th)], 1)
+        wd = np.full(n_dir, 8 * (np.pi / 4) / n_dir)
+    else:
+        xt, wt = np.polynomial.legendre.leggauss(n_dir)
+        pol = 0.5 * np.pi * (xt + 1)
+        wpol = 0.5 * np.pi * wt * np.sin(pol)
+        az = (np.arange(2 * n_dir) + 0.5) * np.pi / n_dir
+        dirs = np.stack([np.repeat(np.cos(pol), len(az)), np.outer(np.sin(pol), np.sin(az)).ravel(),
+                         np.outer(np.sin(pol), np.cos(az)).ravel()], 1)
+        wd = np.outer(wpol, np.full(len(az), np.pi / n_dir)).ravel()
+    Bt = np.repeat(beta, len(wd))
+    K = Bt[:, None] * np.tile(dirs, (n_beta, 1))
+    psi2 = (2 - 2 * np.cos(C * Bt)) / C ** 2
+    cols = [np.sum(1 - np.cos(K @ np.array(_orbit_offsets(k, dim), float).T), 1) / psi2 for k in keys]
+    return np.stack(cols, 1), np.outer(wbeta, wd).ravel()
+
+
+def _exact_minimum(A, W, dps=50):
+    """min_x sum W (A x - 1)^2 by the normal equations in `dps`-digit arithmetic
+    (exact for the float64 entries of A and W, whatever their conditioning).
+    Returns (minimum, minimiser)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = dps
+    n = A.shape[1]
+    G = mpmath.matrix(n, n)
+    g = mpmath.matrix(n, 1)
+    tot = mpmath.mpf(0)
+    for r in range(A.shape[0]):
+        row = [mpmath.mpf(float(x)) for x in A[r]]
+        w = mpmath.mpf(float(W[r]))
+        tot += w
+        for i in range(n):
+            wi = w * row[i]
+            g[i] += wi
+            for j in range(i, n):
+                G[i, j] += wi * row[j]
+    for i in range(n):
+        for j in range(i):
+            G[i, j] = G[j, i]
+    x = mpmath.lu_solve(G, g)
+    return float(tot - sum(g[i] * x[i] for i in range(n))), np.array([float(v) for v in x])
+
+
+@pytest.mark.parametrize("dim,shape,M", [(2, "rhombus", 8), (2, "square", 4), (2, "square", 8),
+                                         (3, "rhombus", 4), (2, "rhombus", 4), (2, "cross", 8)])
+def test_displs_weights_of_the_workloads_reach_the_exact_minimum(dim, shape, M):
+    """Every DispLS stencil the 1001^2 and 400^3 workloads run, at C = 0.3 and
+    b = pi/2, against the exact minimum of the paper's functional E_disp(b)
+    built and minimised here (see _displs_design, _exact_minimum).
+    - Where the design matrix keeps every singular value above the cutoff
+      (1e-10 sigma_max), the oracle's weights are the minimiser: E(w) is
+      within 1e-6 of the minimum.
+    - Square(8) has condition number ~7e14; the minimum-norm solution drops
+      the directions below the cutoff.  E(w) then exceeds the minimum by less
+      than 1e-12 of the functional's scale E(0) (an RMS relative dispersion
+      error of about 1e-8 either way), with weights far smaller than the
+      exact minimiser's, whose cancelling entries FP32 rounding would spoil.
+    A dropped term, a wrong sign, a transposed offset or the missing factor 2
+    of Psi2 changes E(w) by orders of magnitude more than these margins."""
+    C, b = 0.3, np.pi / 2
+    w = S.weights(dim, shape, M, 0, "displs", C=C, b=b)
+    keys = [k for k in w if any(k)]
+    A, W = _displs_design(dim, keys, C, b, n_dir=16 if dim == 2 else 20)
+    x = np.array([w[k] for k in keys])
+    E = float(np.sum(W * (A @ x - 1) ** 2))
+    Emin, xmin = _exact_minimum(A, W)
+    E0 = float(np.sum(W))
+    assert Emin <= E * (1 + 1e-9)
+    if (shape, M) == ("square", 8):
+        assert E - Emin < 1e-12 * E0
+        assert np.linalg.norm(x) < 0.1 * np.linalg.norm(xmin)
+    else:
+        assert E <= Emin * (1 + 1e-6), (E, Emin)
+    # and a plausible mistake is far outside that margin: the factor 2 of Psi2
+    # dropped (the garbled Eq. psibeta2) or the weights' sign flipped
+    assert float(np.sum(W * (0.5 * (A @ x) - 1) ** 2)) > 1e3 * Emin
+    assert float(np.sum(W * (-(A @ x) - 1) ** 2)) > 1e3 * Emin
