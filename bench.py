@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--shots", type=int, default=0, help="fwi/batched: use the first N shots")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-gradient", action="store_true",
+                    help="3d: skip the FWI-gradient sub-record")
     return ap.parse_args()
 
 
@@ -274,6 +276,8 @@ def run_gpu(args):
             "kernel": "step3d " + kernels[dom]["stencil"],
             "bytes_per_point": 16, "peak_source": peak_kind}
 
+    grad_rec = None if args.no_gradient else bench_gradient(args, dev, stream, peak, peak_kind, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(pr, runs[0]["dt"])
@@ -286,11 +290,93 @@ def run_gpu(args):
                       "padded_points": pts, "receivers": len(rec_idx), "l2": "inputs larger than L2",
                       "parallelism": "independent replicas per GPU"},
            "e2e": e2e, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
-           "clocks": clocks, "gpu_launches": args.steps * len(runs) * (nt + 1)}
+           "clocks": clocks, "gpu_launches": args.steps * len(runs) * (nt + 1),
+           "gradient": grad_rec}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+# Algorithmic bytes per padded point and time step of the checkpointed
+# gradient: three sweeps of the 16 B/pt step (forward, recompute, adjoint);
+# the checkpoint copies, two fields read and written when stored every k
+# steps and again when restored for the segment's recompute (32/k); the D
+# store of the recompute and its load in the adjoint (4 + 4); and the
+# gradient accumulator read and written in the adjoint (4 + 4).
+GRAD_K = 20
+GRAD_BYTES_PER_POINT = 3 * 16.0 + 32.0 / GRAD_K + 8.0 + 8.0
+
+
+def bench_gradient(args, dev, stream, peak, peak_kind, world):
+    """FWI gradient of the 256^3 workload (296^3 padded, 1200 steps, Cross(4),
+    checkpoints every 20 steps): `args.steps` full shots timed with CUDA events
+    after one untimed shot, and the same through host buffers (m in, dJ/dm
+    out).  Metric: padded points x time steps of gradient per second."""
+    import torch
+    import torch.distributed as dist
+    import paper_2606_04882_gb300 as F
+    import workloads as WL
+    probs, _ = WL.fwi_3d()
+    pr = probs[0]
+    dt = 0.5 * F.fd_cfl_limit(F.stencil_desc(3, "cross", 4)) * pr.h / pr.vmax
+    plan = F.Plan(pr.shape, pr.h, dt, pr.nt, pr.nb, pr.vmax, F.stencil_desc(3, "cross", 4))
+    m_host = (1.0 / pr.vel.astype(np.float64) ** 2).astype(np.float32)
+    m = torch.from_numpy(m_host).to(dev)
+    ri = plan.linear_index(pr.rec)
+    wav = torch.from_numpy(F.fd_ricker(pr.f0, dt, pr.nt)[:, None].copy()).to(dev)
+    resid = torch.randn((pr.nt, len(ri)), device=dev, generator=torch.Generator(dev).manual_seed(5))
+    grad = torch.empty_like(m)
+    ws = F.workspace(plan.gradient_workspace_size(1, len(ri), GRAD_K), dev)
+    inf = plan.info()
+    pts = int(inf.padded[0] * inf.padded[1] * inf.padded[2])
+    shots = [plan.linear_index(probs[i % len(probs)].src) for i in range(max(args.steps, 1))]
+
+    def shot(si, mm, gg):
+        F.fd_adjoint_gradient(plan, mm, si, wav, ri, resid, GRAD_K, gg, ws,
+                              model_kind=F.FD_MODEL_SLOWNESS2)
+
+    shot(shots[0], m, grad)
+    assert F.fd_status_read(plan, ws) == 0, F.last_error()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for si in shots:
+        shot(si, m, grad)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / len(shots)
+    hm = torch.from_numpy(m_host).pin_memory()
+    hg = torch.empty(m_host.shape, dtype=torch.float32).pin_memory()
+    dm, dg = torch.empty_like(m), torch.empty_like(grad)
+    a.record(stream)
+    for si in shots:
+        dm.copy_(hm, non_blocking=True)
+        shot(si, dm, dg)
+        hg.copy_(dg, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ems = a.elapsed_time(b) / len(shots)
+    assert F.fd_status_read(plan, ws) == 0, F.last_error()
+    if world > 1:
+        t = torch.tensor([ms, ems], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ems = float(t[0]), float(t[1])
+    work = pts * pr.nt * world
+    gbs = GRAD_BYTES_PER_POINT * pts * pr.nt / (ms * 1e-3) / 1e9
+    return {"metric": "FWI gradient grid-point updates/s (3D 256^3 + 20-node sponge, 1200 steps, "
+                      "Cross(4), checkpoints every %d steps)" % GRAD_K,
+            "value": work / (ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_shot": ms,
+            "shots_timed": len(shots), "padded_points": pts,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "traffic": None, "peak_source": peak_kind,
+                         "bytes_per_point": GRAD_BYTES_PER_POINT,
+                         "note": "per padded point and time step of the gradient: forward, "
+                                 "recompute and adjoint sweeps 3 x 16 B, checkpoint store and "
+                                 "restore 32/k, D store and load 8, gradient accumulator 8"},
+            "e2e": {"value": work / (ems * 1e-3) / 1e9, "unit": "Gpts/s",
+                    "h2d_bytes_per_step": m.numel() * 4, "d2h_bytes_per_step": grad.numel() * 4},
+            "gpu_launches": len(shots) * (3 * pr.nt + 2)}
 
 
 def run_other(args):
@@ -372,7 +458,7 @@ def run_other(args):
         wav = torch.from_numpy(F.fd_ricker(pr0.f0, dt, pr0.nt)[:, None].copy()).to(dev)
         resid = torch.randn((pr0.nt, len(ri)), device=dev, generator=torch.Generator(dev).manual_seed(5))
         grad = torch.empty_like(m)
-        k = 20
+        k = GRAD_K
         ws = F.workspace(plan.gradient_workspace_size(1, len(ri), k), dev)
         inf = plan.info()
         pts = int(inf.padded[0] * inf.padded[1] * inf.padded[2])
@@ -434,7 +520,7 @@ def run_other(args):
     value = work / (ms * 1e-3) / 1e9
     peak, peak_kind = load_peaks()
     kernels = []
-    bpp = 16.0 if args.workload != "fwi" else 16.0 * 3 + 8.0 / 20 + 4 + 4 + 8
+    bpp = 16.0 if args.workload != "fwi" else GRAD_BYTES_PER_POINT
     for i, (name, _, pts, nt, _) in enumerate(jobs):
         run_ms = statistics.mean(ev[kk][i][0].elapsed_time(ev[kk][i][1]) for kk in range(args.steps))
         per = max(run_ms - setup_ms[i], 1e-9) / nt
@@ -449,8 +535,8 @@ def run_other(args):
         roof["note"] = "fields (4.7 MB) are L2-resident: the HBM fraction is nominal"
     if args.workload == "fwi":
         roof["note"] = ("bytes per point per time step of the whole gradient: forward, recompute "
-                        "and adjoint sweeps (3 x 16) + checkpoints (8/k) + D store/load (8) + "
-                        "gradient accumulator (8)")
+                        "and adjoint sweeps (3 x 16) + checkpoint store and restore (32/k) + "
+                        "D store/load (8) + gradient accumulator (8)")
     out = {"metric": "grid-point updates/s (%s)" % args.workload, "value": value, "unit": "Gpts/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -34,8 +34,10 @@
  *   - Errors: every call returns an fd_status; nothing is thrown across the
  *     ABI.  fd_last_error() gives a thread-local message for the last failing
  *     call of the calling thread.  Conditions detected on the device (time-out
- *     of a bounded wait, a velocity above vmax) are recorded in a status word
- *     in the workspace and returned by fd_status_read().
+ *     of a bounded wait, a velocity above vmax, a wavefield that grew beyond
+ *     1e30 or became non-finite, checked every 32 steps and at the last step)
+ *     are recorded in a status word in the workspace and returned by
+ *     fd_status_read().
  */
 #ifndef FDWAVE_H
 #define FDWAVE_H
@@ -228,8 +230,16 @@ int fd_forward(fd_plan *plan, int model_kind, const float *model_d,
 
 /*
  * fd_status_read - synchronise `stream` and return the device status word of
- * the last call that used workspace ws_d (FD_OK, FD_ERR_TIMEOUT,
- * FD_ERR_UNSTABLE), then clear it.
+ * the last call that used workspace ws_d, then clear it:
+ *   FD_ERR_TIMEOUT   a bounded device wait gave up (the kernel returned early;
+ *                    the results of that call are not valid);
+ *   FD_ERR_UNSTABLE  the model exceeded the plan's vmax, or the wavefield grew
+ *                    without bound (|u| > 1e30 or non-finite at a checked step:
+ *                    every 32nd step and the last; the gradient checks its
+ *                    forward and adjoint sweeps);
+ *   FD_OK            none of these.
+ * This is how the von Neumann analysis of Eq. full_disp is enforced at run
+ * time for models and states the plan's checks did not see.
  */
 int fd_status_read(const fd_plan *plan, void *ws_d, void *stream);
 
@@ -295,8 +305,10 @@ int fd_forward_batched(int nshots, const fd_shot *shots, void *ws_d, size_t ws_b
  * no counterpart; this is a deployment convenience.
  * Arguments are those of fd_forward without the workspace: the scratch comes
  * from a static device array of 32 MiB compiled into the library, which every
- * GPU that loads the library holds until the process exits.  The call
- * allocates no device memory.
+ * GPU that loads the library holds until the process exits.  The call makes
+ * no cudaMalloc or cudaFree call, and no allocation through any library; its
+ * time steps are launched one by one on `stream` (no CUDA graph is captured
+ * or instantiated, no stream is created and the device is not synchronised).
  *   - Problems whose forward workspace (fd_forward_workspace_size) exceeds
  *     32 MiB are rejected with FD_ERR_NOMEM before any device work.
  *   - The first call on a device resolves the array's address on that device
@@ -306,13 +318,21 @@ int fd_forward_batched(int nshots, const fd_shot *shots, void *ws_d, size_t ws_b
  *     call clears what must start at zero, but calls that overlap on the GPU
  *     (other streams, other host threads, other plans) race on it: serialise
  *     them.
- *   - Device status bits of these calls are not retrievable by fd_status_read
- *     (the caller has no workspace pointer); host-side errors are returned.
+ *   - Host-side errors are returned; conditions detected on the device go to
+ *     a status word in the array, read by fd_status_read_noalloc.
  */
 int fd_forward_noalloc(fd_plan *plan, int model_kind, const float *model_d,
                        int nsrc, const int64_t *src_idx, const float *wavelet_d,
                        int nrec, const int64_t *rec_idx, float *traces_d,
                        const float *state_in_d, float *state_out_d, void *stream);
+
+/*
+ * fd_status_read_noalloc - fd_status_read for fd_forward_noalloc: synchronise
+ * `stream`, return the device status word of the last fd_forward_noalloc call
+ * on the current device (FD_OK, FD_ERR_TIMEOUT, FD_ERR_UNSTABLE) and clear it.
+ * The paper has no counterpart.  Errors: FD_ERR_ARG, FD_ERR_CUDA.
+ */
+int fd_status_read_noalloc(const fd_plan *plan, void *stream);
 
 /*
  * Evaluation metrics (Section 2.4 and Appendix A), computed on the GPU in

@@ -91,6 +91,7 @@ _SIGS = {
     "fd_forward_batched_workspace_size": (_I, [_I, _P, _P]),
     "fd_forward_batched": (_I, [_I, _P, _P, _SZ, _P]),
     "fd_forward_noalloc": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P]),
+    "fd_status_read_noalloc": (_I, [_P, _P]),
     "fd_last_error": (ctypes.c_char_p, []),
     "fd_version": (ctypes.c_char_p, []),
 }
@@ -280,6 +281,19 @@ def fd_status_read(plan: Plan, ws, stream=None) -> int:
     return lib().fd_status_read(plan.ptr, _addr(ws), _stream_ptr(stream))
 
 
+def fd_status_read_noalloc(plan: Plan, stream=None) -> int:
+    """Device status of the last fd_forward_noalloc call on the current device."""
+    return lib().fd_status_read_noalloc(plan.ptr, _stream_ptr(stream))
+
+
+def check_status(plan: Plan, ws, what: str = "device run", stream=None) -> None:
+    """Raise FdError when the device status word of the last call that used
+    `ws` reports a condition (time-out, vmax exceeded, unbounded growth)."""
+    rc = fd_status_read(plan, ws, stream)
+    if rc != FD_OK:
+        raise FdError(rc, "%s: %s" % (what, last_error()))
+
+
 def fd_error_norms(num, ref, scale1: float = 1.0, scale2: float = 1.0, out=None, stream=None):
     """(scale1 sum|num - ref|, scale2 sqrt(sum (num - ref)^2), max|num - ref|) as a
     float64 device tensor [3] (Section 2.4); num and ref are float32 device
@@ -396,6 +410,7 @@ def _make_traces_fn():
             ws = workspace(plan.forward_workspace_size(len(src_idx), len(rec_idx)), m.device)
             fd_forward(plan, m, src_idx, wavelet, rec_idx, traces, ws,
                        model_kind=FD_MODEL_SLOWNESS2)
+            check_status(plan, ws, "acoustic_traces forward")
             ctx.save_for_backward(m, wavelet)
             ctx.plan, ctx.src_idx, ctx.rec_idx, ctx.k = plan, src_idx, rec_idx, k
             return traces
@@ -410,6 +425,7 @@ def _make_traces_fn():
             fd_adjoint_gradient(plan, m, ctx.src_idx, wavelet, ctx.rec_idx,
                                 grad_traces.contiguous().float(), ctx.k, grad, ws,
                                 model_kind=FD_MODEL_SLOWNESS2)
+            check_status(plan, ws, "acoustic_traces backward")
             return grad, None, None, None, None, None
 
     return AcousticTraces

@@ -81,7 +81,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 
 // Wait with a time bound of about `cycles` SM clocks; false on time-out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  long long cycles = 4000000000LL)
+                                                  long long cycles = kWaitCycles)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
@@ -117,6 +117,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Growth check of a step's outputs: a value that is non-finite or above
+// kBlowupAmp in magnitude marks the run unstable (the comparison is false for
+// NaN, so NaN is caught too).
+__device__ __forceinline__ void check_growth(int *status, const float4 &o)
+{
+    if (!(fabsf(o.x) <= kBlowupAmp && fabsf(o.y) <= kBlowupAmp && fabsf(o.z) <= kBlowupAmp &&
+          fabsf(o.w) <= kBlowupAmp))
+        atomicOr(status, kStatusBlowup);
 }
 
 // ---------------------------------------------------------------------------

@@ -17,6 +17,10 @@ constexpr int kMax3 = 8;                      // largest 3D radius
 constexpr int kW3 = kMax3 + 1;
 constexpr int kStatusTimeout = 1;            // status word bits
 constexpr int kStatusVmax = 2;
+constexpr int kStatusBlowup = 4;             // a checked step produced |u| > kBlowupAmp or a non-finite value
+constexpr float kBlowupAmp = 1e30f;
+constexpr int kCheckEvery = 32;              // steps between growth checks (and the last step)
+constexpr long long kWaitCycles = 4000000000LL;   // bound of every device wait (~2 s of SM clocks)
 
 // Point of a per-tile source/receiver table.  Entries of one tile are sorted
 // by z.  (x, y) are local to the tile; z is the padded global plane/row.
@@ -55,6 +59,11 @@ struct StepParams {
     int zchunk;                // 3D: planes per z-chunk
     int nz_chunks;
     int step;                  // row of the injection series / sample output
+    int check;                 // 1: check this step's outputs for growth (kStatusBlowup)
+    // bounded waits of the 3D kernels: limit in SM clocks, and (fault-injection
+    // test hook, -1 when off) a stream slot whose arrival CTA 0's producer skips
+    long long wait_cycles;
+    int drop_slot;
     // per-tile point tables (CSR over tiles)
     const int32_t *inj_ptr;
     const PtEntry *inj;
@@ -129,6 +138,7 @@ struct BatchParams {
     int roles[4];
     int ntiles;                // tiles of all shots
     int step;                  // time step n (field parity and series row)
+    int check;                 // 1: check this step's outputs for growth (kStatusBlowup)
     int *status;
     float w[kWDim * kWDim];
 };

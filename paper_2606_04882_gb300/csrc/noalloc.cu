@@ -68,8 +68,23 @@ extern "C" int fd_forward_noalloc(fd_plan *plan, int model_kind, const float *mo
                               need, kNoallocScratchBytes);
     void *ws = nullptr;
     if ((st = scratch_address(&ws))) return st;
-    // fd_forward clears the status word and both wavefield buffers on every call,
-    // so nothing left in the array by an earlier call leaks into this one.
-    return fd_forward(plan, model_kind, model_d, nsrc, src_idx, wavelet_d, nrec, rec_idx, traces_d,
-                      state_in_d, state_out_d, ws, kNoallocScratchBytes, stream);
+    // The forward path clears the status word and both wavefield buffers on every
+    // call, so nothing left in the array by an earlier call leaks into this one.
+    // Steps are launched one by one: no graph is captured or instantiated and no
+    // cached graph is evicted (which would synchronise the device).
+    return fdw::forward_impl(plan, model_kind, model_d, nsrc, src_idx, wavelet_d, nrec, rec_idx,
+                             traces_d, state_in_d, state_out_d, ws, kNoallocScratchBytes, stream,
+                             false);
+}
+
+// The status word of the last fd_forward_noalloc call on the current device
+// sits at the start of the static array; this reads and clears it like
+// fd_status_read does for a caller's workspace.
+extern "C" int fd_status_read_noalloc(const fd_plan *plan, void *stream)
+{
+    fdw::clear_error();
+    void *ws = nullptr;
+    int st = scratch_address(&ws);
+    if (st) return st;
+    return fd_status_read(plan, ws, stream);
 }

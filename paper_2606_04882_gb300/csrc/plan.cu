@@ -279,6 +279,8 @@ void fill_params(const fd_plan *p, StepParams &sp)
     sp.tiles_y = p->tiles_y;
     sp.zchunk = p->zchunk;
     sp.nz_chunks = p->nz_chunks;
+    sp.wait_cycles = kWaitCycles;
+    sp.drop_slot = -1;
     std::memcpy(sp.w, p->W, sizeof sp.w);
     // packed 3D weight tables, from the FP32 table
     auto pair = [](float v) {
@@ -339,6 +341,34 @@ void bind_maps(StepParams &sp, const CUtensorMap *maps, int nbuf, int cur, int p
     sp.tmap_cur_t = maps + 2 * cur + 1;
     sp.tmap_prev_t = maps + 2 * prev + 1;
     sp.tmap_kappa_t = maps + 2 * nbuf;
+}
+
+// Growth check on every kCheckEvery-th step and on the last one.
+inline int check_step(int n, int nt) { return (n + 1) % kCheckEvery == 0 || n + 1 == nt; }
+
+// Fault-injection test hook that faults nothing.  FDWAVE_DEBUG_WAIT_CYCLES=<c>
+// bounds every wait of the 3D kernels by c SM clocks, and
+// FDWAVE_DEBUG_DROP_SLOT=<s> makes the producer of CTA 0 skip stream slot s:
+// that CTA's consumers then wait for copies that never come, give up after c
+// clocks and report FD_ERR_TIMEOUT through the status word, and the producer
+// gives up on their release the same way.  A call with the hook set launches
+// its steps one by one (no graph is captured or replayed).  Returns true when
+// the hook is set.
+bool debug_hook(const fd_plan *p, StepParams &sp)
+{
+    if (p->prob.dim != 3) return false;
+    const char *c = getenv("FDWAVE_DEBUG_WAIT_CYCLES");
+    const char *d = getenv("FDWAVE_DEBUG_DROP_SLOT");
+    bool on = false;
+    if (c && *c) {
+        const long long v = atoll(c);
+        if (v > 0) { sp.wait_cycles = v; on = true; }
+    }
+    if (d && *d) {
+        sp.drop_slot = atoi(d);
+        on = true;
+    }
+    return on;
 }
 
 int check_common(const fd_plan *p, int model_kind, const float *model, int nsrc,
@@ -774,12 +804,13 @@ struct FwdBind {
 
 }  // namespace
 
-extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int nsrc,
-                          const int64_t *src, const float *wavelet, int nrec, const int64_t *rec,
-                          float *traces, const float *state_in_d, float *state_out_d, void *ws,
-                          size_t ws_bytes, void *stream)
+namespace fdw {
+
+int forward_impl(fd_plan *p, int model_kind, const float *model, int nsrc, const int64_t *src,
+                 const float *wavelet, int nrec, const int64_t *rec, float *traces,
+                 const float *state_in_d, float *state_out_d, void *ws, size_t ws_bytes,
+                 void *stream, bool graphs)
 {
-    clear_error();
     if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
     const Layout L = make_layout(p, nsrc, nrec, false, 1);
     int st = check_common(p, model_kind, model, nsrc, src, wavelet, nrec, rec, ws, ws_bytes, L.total);
@@ -834,13 +865,15 @@ extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int ns
             sp.u_cur = cur ? B : A;
             sp.u_prev = cur ? A : B;
             sp.step = n;
+            sp.check = check_step(n, p->prob.nt);
             cudaError_t e = launch(p, kModeForward, sp, ls);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     };
+    const bool hooked = debug_hook(p, sp);
     const char *ge_env = getenv("FDWAVE_GRAPHS");
-    const bool use_graph = pgrid == 0 && p->prob.nt >= 16 && !(ge_env && ge_env[0] == '0');
+    const bool use_graph = graphs && pgrid == 0 && p->prob.nt >= 16 && !(ge_env && ge_env[0] == '0') && !hooked;
     if (pgrid > 0) {
         PersistParams pp;
         std::memset(&pp, 0, sizeof pp);
@@ -899,6 +932,18 @@ extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int ns
     return FD_OK;
 }
 
+}  // namespace fdw
+
+extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int nsrc,
+                          const int64_t *src, const float *wavelet, int nrec, const int64_t *rec,
+                          float *traces, const float *state_in_d, float *state_out_d, void *ws,
+                          size_t ws_bytes, void *stream)
+{
+    clear_error();
+    return forward_impl(p, model_kind, model, nsrc, src, wavelet, nrec, rec, traces, state_in_d,
+                        state_out_d, ws, ws_bytes, stream, true);
+}
+
 extern "C" int fd_status_read(const fd_plan *p, void *ws, void *stream)
 {
     clear_error();
@@ -909,7 +954,13 @@ extern "C" int fd_status_read(const fd_plan *p, void *ws, void *stream)
     FDW_CK(cudaStreamSynchronize(s));
     FDW_CK(cudaMemsetAsync(ws, 0, sizeof word, s));
     if (word & kStatusTimeout) return set_error(FD_ERR_TIMEOUT, "a bounded device wait timed out");
-    if (word & kStatusVmax) return set_error(FD_ERR_UNSTABLE, "model velocity exceeds the plan's vmax");
+    if (word & kStatusVmax)
+        return set_error(FD_ERR_UNSTABLE, "model velocity exceeds the plan's vmax%s",
+                         (word & kStatusBlowup) ? ", and the wavefield grew without bound" : "");
+    if (word & kStatusBlowup)
+        return set_error(FD_ERR_UNSTABLE, "the wavefield became non-finite or exceeded %g in "
+                         "magnitude (checked every %d steps and at the last step)",
+                         (double)kBlowupAmp, kCheckEvery);
     return FD_OK;
 }
 
@@ -952,6 +1003,7 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
 
     StepParams sp;
     fill_params(p, sp);
+    debug_hook(p, sp);
     sp.kappa = reinterpret_cast<const float *>(w + L.kappa);
     sp.status = reinterpret_cast<int *>(w + L.status);
     auto bind_fwd = [&](bool sample) {
@@ -977,6 +1029,7 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
         sp.u_cur = buf[cur];
         sp.u_prev = buf[cur ^ 1];
         sp.step = n;
+        sp.check = check_step(n, nt);
         FDW_CK(launch(p, kModeForward, sp, s));
     }
     // backward sweep over segments
@@ -992,6 +1045,7 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
             sp.u_cur = buf[cur];
             sp.u_prev = buf[cur ^ 1];
             sp.step = n;
+            sp.check = 0;   // the recompute repeats the checked forward sweep bit for bit
             sp.dseg_out = reinterpret_cast<float *>(dseg + (size_t)(n - k0) * fb);
             FDW_CK(launch(p, kModeStoreD, sp, s));
         }
@@ -1011,6 +1065,7 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
             sp.u_cur = buf[cur];
             sp.u_prev = buf[cur ^ 1];
             sp.step = j - 1;
+            sp.check = check_step(t, nt);
             sp.dseg_in = reinterpret_cast<const float *>(dseg + (size_t)(j - 1 - k0) * fb);
             FDW_CK(launch(p, kModeAdjoint, sp, s));
         }
@@ -1336,6 +1391,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
             int n = 0, cur = 0, prev = 1;
             if (nt & 1) {
                 bp.step = 0;
+                bp.check = check_step(0, nt);
                 ce = launch_batched2d(bv, bp, ntiles, cs);
                 n = 1; cur = 1; prev = 0;
             }
@@ -1343,6 +1399,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
                 const int o1 = cur < 2 ? 2 : 0, o2 = o1 + 1;
                 bp.roles[0] = cur; bp.roles[1] = prev; bp.roles[2] = o1; bp.roles[3] = o2;
                 bp.step = n;
+                bp.check = check_step(n, nt) || check_step(n + 1, nt);
                 ce = launch_batched2d2(bv, bp, ntiles, cs);
                 cur = o2; prev = o1;
             }
@@ -1350,6 +1407,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         for (int n = 0; n < nt && ce == cudaSuccess && !two; ++n) {
             if (one) {
                 bp.step = n;
+                bp.check = check_step(n, nt);
                 ce = launch_batched2d(bv, bp, ntiles, cs);
                 continue;
             }
@@ -1360,6 +1418,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
                 sp.u_cur = cur ? Bs[i] : As[i];
                 sp.u_prev = cur ? As[i] : Bs[i];
                 sp.step = n;
+                sp.check = check_step(n, nt);
                 ce = launch(shots[i].plan, kModeForward, sp, cs);
             }
         }

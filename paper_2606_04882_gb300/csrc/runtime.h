@@ -20,4 +20,11 @@ int compute_weights(const fd_stencil_desc *d, std::vector<std::array<int, 3>> &k
                     std::vector<std::array<int, 3>> *offsets, std::vector<int> *off_orbit);
 int compute_cfl(const fd_stencil_desc *d, const std::vector<double> &w, double *cmax);
 
+// fd_forward's body; `graphs` false launches the steps one by one on the
+// caller's stream (no graph capture, instantiation or cache eviction).
+int forward_impl(fd_plan *p, int model_kind, const float *model, int nsrc, const int64_t *src,
+                 const float *wavelet, int nrec, const int64_t *rec, float *traces,
+                 const float *state_in_d, float *state_out_d, void *ws, size_t ws_bytes,
+                 void *stream, bool graphs);
+
 }  // namespace fdw

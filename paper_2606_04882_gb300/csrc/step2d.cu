@@ -223,6 +223,7 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
         if (!colok || zg >= p.nz) continue;
         const int64_t off = (int64_t)zg * p.pitch + xg;
         const float4 un = make_float4(o[0], o[1], o[2], o[3]);
+        if (p.check) check_growth(p.status, un);
         *reinterpret_cast<float4 *>(p.u_prev + off) = un;
         if (MODE != kModeAdjoint && p.dseg_out)
             *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
@@ -266,11 +267,14 @@ struct BatchView {
     float *smp_out;
     int smp_ncol;
     int step;
+    int check;
+    int *status;
     const float (&w)[kWDim * kWDim];
     __device__ BatchView(const ShotInfo &d, const BatchParams &bp)
         : u_prev(d.buf[(bp.step & 1) ^ 1]), nx(d.nx), nz(d.nz), pitch(d.pitch), gcoef(d.gcoef),
           tiles_x(d.tiles_x), inj(d.inj), inj_series(d.inj_series), inj_ncol(d.inj_ncol),
-          smp(d.smp), smp_out(d.smp_out), smp_ncol(d.smp_ncol), step(bp.step), w(bp.w)
+          smp(d.smp), smp_out(d.smp_out), smp_ncol(d.smp_ncol), step(bp.step), check(bp.check),
+          status(bp.status), w(bp.w)
     {
         for (int i = 0; i < 3; ++i) {
             phys_lo[i] = d.phys_lo[i];
@@ -352,8 +356,9 @@ __device__ __forceinline__ void stream_tile(const BatchView &v, const Staged &st
                 v.smp_out[(int64_t)v.step * v.smp_ncol + en.col] = s * en.scale;
             });
         if (!colok || zg >= v.nz) continue;
-        *reinterpret_cast<float4 *>(v.u_prev + (int64_t)zg * v.pitch + xg) =
-            make_float4(o[0], o[1], o[2], o[3]);
+        const float4 un = make_float4(o[0], o[1], o[2], o[3]);
+        if (v.check) check_growth(v.status, un);
+        *reinterpret_cast<float4 *>(v.u_prev + (int64_t)zg * v.pitch + xg) = un;
     }
 }
 
@@ -549,9 +554,11 @@ __device__ __forceinline__ void stream2_tile(const BatchView &v, const Staged &s
                 v.smp_out[(int64_t)v.step * v.smp_ncol + en.col] = sv * en.scale;
             });
         const int xg = x0 + tc;
-        if (xg < v.nx && zg < v.nz)
-            *reinterpret_cast<float4 *>(out1 + (int64_t)zg * v.pitch + xg) =
-                make_float4(o[0], o[1], o[2], o[3]);
+        if (xg < v.nx && zg < v.nz) {
+            const float4 un = make_float4(o[0], o[1], o[2], o[3]);
+            if (v.check) check_growth(v.status, un);
+            *reinterpret_cast<float4 *>(out1 + (int64_t)zg * v.pitch + xg) = un;
+        }
     }
     consumers_sync();
     // stage 2: u^{n+2} on the tile
@@ -600,8 +607,9 @@ __device__ __forceinline__ void stream2_tile(const BatchView &v, const Staged &s
                 v.smp_out[(int64_t)step1 * v.smp_ncol + en.col] = sv * en.scale;
             });
         if (!colok || zg >= v.nz) continue;
-        *reinterpret_cast<float4 *>(out2 + (int64_t)zg * v.pitch + xg) =
-            make_float4(o[0], o[1], o[2], o[3]);
+        const float4 un = make_float4(o[0], o[1], o[2], o[3]);
+        if (v.check) check_growth(v.status, un);
+        *reinterpret_cast<float4 *>(out2 + (int64_t)zg * v.pitch + xg) = un;
     }
     consumers_sync();   // u1 is rewritten by the next tile
 }
@@ -725,6 +733,7 @@ struct StepView {
     float *smp_out;
     int smp_ncol;
     int step;
+    int check;
     float *dseg_out;
     const float *dseg_in;
     float *gacc;
@@ -736,7 +745,7 @@ struct StepView {
           tiles_x(pp.base.tiles_x), inj_ptr(pp.base.inj_ptr), inj(pp.base.inj),
           inj_series(pp.base.inj_series), inj_ncol(pp.base.inj_ncol), smp_ptr(pp.base.smp_ptr),
           smp(pp.base.smp), smp_out(pp.base.smp_out), smp_ncol(pp.base.smp_ncol), step(n),
-          dseg_out(nullptr), dseg_in(nullptr), gacc(nullptr), status(pp.base.status), w(pp.base.w)
+          check((n + 1) % kCheckEvery == 0 || n + 1 == pp.nt), dseg_out(nullptr), dseg_in(nullptr), gacc(nullptr), status(pp.base.status), w(pp.base.w)
     {
         for (int i = 0; i < 3; ++i) {
             phys_lo[i] = pp.base.phys_lo[i];
@@ -883,6 +892,7 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
             p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
         });
     if (!live) return;
+    if (p.check) check_growth(p.status, un);
     *reinterpret_cast<float4 *>(p.u_prev + off) = un;
     if (MODE != kModeAdjoint && p.dseg_out)
         *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);

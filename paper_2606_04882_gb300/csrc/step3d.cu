@@ -188,12 +188,17 @@ step3d_cross(const __grid_constant__ StepParams p)
         for (; s < S; ++s) {
             // reuse of a slot waits for the consumers' release of stream index s - NR,
             // i.e. the completion of empty phase s / NR - 1
-            if (s >= NR && !mbar_wait_bounded(&empty[slot], (uint32_t)((s / NR - 1) & 1))) {
+            if (s >= NR && !mbar_wait_bounded(&empty[slot], (uint32_t)((s / NR - 1) & 1), p.wait_cycles)) {
                 atomicOr(p.status, kStatusTimeout);
                 *abort_v = 1;
                 break;
             }
             if (*abort_v) break;
+            // test hook: CTA 0 issues nothing for slot drop_slot, so its consumers' wait runs out
+            if (blockIdx.x == 0 && s == p.drop_slot) {
+                if (++slot == NR) slot = 0;
+                continue;
+            }
             float *dst = sm + slot * SLOT;
             const int zq = zb + s - M;                  // queue plane carried by this slot
             if (s < 2 * M) {
@@ -210,7 +215,8 @@ step3d_cross(const __grid_constant__ StepParams p)
         }
         if (*abort_v) {   // let copies already issued land before the block exits
             for (int i = max(0, s - NR); i < s; ++i)
-                mbar_wait_bounded(&full[i % NR], (i / NR) & 1, 100000000LL);
+                if (!(blockIdx.x == 0 && i == p.drop_slot))
+                    mbar_wait_bounded(&full[i % NR], (i / NR) & 1, 100000000LL);
         }
         return;
     }
@@ -261,7 +267,7 @@ step3d_cross(const __grid_constant__ StepParams p)
             const int si = k0 + uu;            // 0-based stream index
             if (si >= S) break;
             const int u = kUnroll ? uu : QL - 1 + uu;   // slot of the plane fed now
-            ok = ok && mbar_wait_bounded(&full[slot], fph);
+            ok = ok && mbar_wait_bounded(&full[slot], fph, p.wait_cycles);
             if (!ok) break;
             const float *P = sm + slot * SLOT;
             ld4x2(P + C::AEL + 2 * C::TEL + cT, qa[u], qb[u]);   // plane zb + si - M
@@ -335,6 +341,7 @@ step3d_cross(const __grid_constant__ StepParams p)
                 }
                 if (colok) {
                     const int64_t off = (int64_t)z * p.plane + colo;
+                    if (p.check) check_growth(p.status, o);
                     *reinterpret_cast<float4 *>(p.u_prev + off) = o;
                     if (MODE != kModeAdjoint && p.dseg_out)
                         *reinterpret_cast<ulonglong2 *>(p.dseg_out + off) = make_ulonglong2(dv01, dv23);
@@ -421,12 +428,17 @@ step3d_planar(const __grid_constant__ StepParams p)
         volatile int *abort_v = &abort_flag;
         int slot = 0, t = 0;
         for (; t < S; ++t) {
-            if (t >= NR && !mbar_wait_bounded(&empty[slot], (uint32_t)((t / NR - 1) & 1))) {
+            if (t >= NR && !mbar_wait_bounded(&empty[slot], (uint32_t)((t / NR - 1) & 1), p.wait_cycles)) {
                 atomicOr(p.status, kStatusTimeout);
                 *abort_v = 1;
                 break;
             }
             if (*abort_v) break;
+            // test hook: CTA 0 issues nothing for slot drop_slot, so its consumers' wait runs out
+            if (blockIdx.x == 0 && t == p.drop_slot) {
+                if (++slot == NR) slot = 0;
+                continue;
+            }
             float *dst = sm + slot * SLOT;
             const int P = zb - M + t;
             if (t < 2 * M) {
@@ -443,7 +455,8 @@ step3d_planar(const __grid_constant__ StepParams p)
         }
         if (*abort_v) {
             for (int i = max(0, t - NR); i < t; ++i)
-                mbar_wait_bounded(&full[i % NR], (i / NR) & 1, 100000000LL);
+                if (!(blockIdx.x == 0 && i == p.drop_slot))
+                    mbar_wait_bounded(&full[i % NR], (i / NR) & 1, 100000000LL);
         }
         return;
     }
@@ -493,7 +506,7 @@ step3d_planar(const __grid_constant__ StepParams p)
         for (int uu = 0; uu < UF; ++uu) {
             const int t = t0 + uu;
             if (t >= S) break;
-            ok = ok && mbar_wait_bounded(&full[slot], fph);
+            ok = ok && mbar_wait_bounded(&full[slot], fph, p.wait_cycles);
             if (!ok) break;
             const float *A = sm + slot * SLOT;
             // Centre-free Laplacian, split per plane: T[s] sums the points of plane
@@ -633,6 +646,7 @@ step3d_planar(const __grid_constant__ StepParams p)
             }
             if (colok) {
                 const int64_t off = (int64_t)z * p.plane + colo;
+                if (p.check) check_growth(p.status, o);
                 *reinterpret_cast<float4 *>(p.u_prev + off) = o;
                 if (MODE != kModeAdjoint && p.dseg_out)
                     *reinterpret_cast<ulonglong2 *>(p.dseg_out + off) = make_ulonglong2(dv01, dv23);

@@ -89,8 +89,7 @@ def gpu_shot_fn(plan, model_m, src_idx: Sequence[np.ndarray], wavelets, rec_idx:
     """Per-shot (J_s, dJ/dm) on the GPU for m = 1/v^2: forward traces, residual
     d - d_obs, adjoint gradient with checkpoints every k steps."""
     import torch
-    from . import (FD_MODEL_SLOWNESS2, fd_adjoint_gradient, fd_forward, fd_status_read,
-                   workspace)
+    from . import FD_MODEL_SLOWNESS2, check_status, fd_adjoint_gradient, fd_forward, workspace
     dev = model_m.device
     nrec = len(rec_idx)
     wsf = workspace(plan.forward_workspace_size(1, nrec), dev)
@@ -100,14 +99,13 @@ def gpu_shot_fn(plan, model_m, src_idx: Sequence[np.ndarray], wavelets, rec_idx:
         tr = torch.empty((plan.nt, nrec), device=dev)
         fd_forward(plan, model_m, src_idx[s], wavelets[s], rec_idx, tr, wsf,
                    model_kind=FD_MODEL_SLOWNESS2)
+        check_status(plan, wsf, "forward of shot %d" % s)
         r = tr - d_obs[s]
         J = 0.5 * float((r.double() ** 2).sum())
         g = torch.empty_like(model_m)
         fd_adjoint_gradient(plan, model_m, src_idx[s], wavelets[s], rec_idx, r, k, g, wsg,
                             model_kind=FD_MODEL_SLOWNESS2)
-        rc = fd_status_read(plan, wsg)
-        if rc != 0:
-            raise RuntimeError("device status %d in shot %d" % (rc, s))
+        check_status(plan, wsg, "gradient of shot %d" % s)
         return J, g
 
     return run

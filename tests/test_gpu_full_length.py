@@ -3,9 +3,12 @@
 The 400^3 forward (460^3 padded, 1500 steps) and the 256^3 FWI gradient
 (296^3 padded, 1200 steps) are compared with oracle runs of the same length
 on the same inputs: relative L2 <= 1e-4 on traces, final wavefields and the
-gradient.  The oracle needs 5 to 20 minutes of all host cores per case, so
-these tests run only with FDWAVE_FULL_LENGTH=1; the default GPU suite checks
-the same workloads at full size through restarts and reduced step counts."""
+gradient, and every receiver's trace on its own (so that one wrong receiver
+among the 10^4 cannot hide under the global norm).  The Cross(4) forward
+(about 5 minutes of 16 host cores for the oracle) runs in the default GPU
+suite; the other three cases take 10 to 20 minutes each and run only with
+FDWAVE_FULL_LENGTH=1 (the default suite checks them at full size through
+restarts and reduced step counts)."""
 import os
 
 import numpy as np
@@ -14,9 +17,9 @@ import pytest
 import workloads as WL
 from gpu_cases import Case, rel_l2
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("FDWAVE_FULL_LENGTH") != "1",
-                                 reason="set FDWAVE_FULL_LENGTH=1 (long oracle runs)")]
+pytestmark = pytest.mark.gpu
+opt_in = pytest.mark.skipif(os.environ.get("FDWAVE_FULL_LENGTH") != "1",
+                            reason="set FDWAVE_FULL_LENGTH=1 (long oracle runs)")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,7 +38,18 @@ def _case(pr, st):
                 src=pr.src, rec=pr.rec, f0=pr.f0, dt=dt)
 
 
-@pytest.mark.parametrize("k", [0, 1, 2])
+def per_receiver_errors(tr, otr):
+    """Relative L2 error of each receiver's trace, with the denominator floored
+    at 1e-3 of the largest trace norm (receivers the wave barely reaches carry
+    FP32 noise of the field around them, not of their own small signal)."""
+    tr = np.asarray(tr, np.float64)
+    otr = np.asarray(otr, np.float64)
+    e = np.linalg.norm(tr - otr, axis=0)
+    o = np.linalg.norm(otr, axis=0)
+    return e / np.maximum(o, 1e-3 * o.max())
+
+
+@pytest.mark.parametrize("k", [0, pytest.param(1, marks=opt_in), pytest.param(2, marks=opt_in)])
 def test_gradient_random_400_full_run(k):
     pr = WL.gradient_random_3d()
     c = _case(pr, pr.stencils[k])
@@ -43,10 +57,15 @@ def test_gradient_random_400_full_run(k):
     assert rc == 0
     otr, ost = c.oracle_forward()
     e_tr, e_u = rel_l2(tr, otr), rel_l2(sf[0], ost[0])
-    print("full-length %s%d: traces %.3g, final field %.3g" % (c.shape, c.M, e_tr, e_u))
+    e_rec = per_receiver_errors(tr, otr)
+    print("full-length %s%d: traces %.3g, final field %.3g, worst receiver %.3g (receiver %d), "
+          "median receiver %.3g" % (c.shape, c.M, e_tr, e_u, e_rec.max(), int(e_rec.argmax()),
+                                    float(np.median(e_rec))))
     assert e_tr < 1e-4 and e_u < 1e-4
+    assert e_rec.max() < 1e-3
 
 
+@opt_in
 def test_fwi_256_full_gradient():
     import torch
     import paper_2606_04882_gb300 as F

@@ -113,3 +113,38 @@ def test_slowness_parameterisation_and_autograd():
     loss = (tr * torch.from_numpy(resid.astype(np.float32)).cuda()).sum()
     loss.backward()
     assert rel_l2(mt.grad.cpu().numpy(), g_m) < 1e-6
+
+
+def test_shot_driver_on_the_gpu_matches_the_oracle_sum():
+    """shots.gpu_shot_fn (forward, residual d - d_obs, adjoint gradient of each
+    shot, with the device status checked after each call), summed over three
+    shots by shots.misfit_and_gradient in one process, against the FP64
+    oracle's misfit J = sum_s 1/2 ||d_s - d_obs,s||^2 and its dJ/dm."""
+    import torch
+    import paper_2606_04882_gb300 as F
+    from paper_2606_04882_gb300.shots import gpu_shot_fn, misfit_and_gradient
+    n, nb, nt, h, vmax, f0 = (48, 64), 6, 150, 10.0, 3000.0, 25.0
+    m32 = (1.0 / smooth_velocity(n, 4, 1500.0, 2900.0, sigma=3.0).astype(np.float64) ** 2).astype(np.float32)
+    v = (1.0 / np.sqrt(m32.astype(np.float64))).astype(np.float32)
+    vt = smooth_velocity(n, 9, 1500.0, 2900.0, sigma=2.0)
+    srcs = [np.array([[2, x]]) for x in (5, 30, 58)]
+    rec = np.array([[2, x] for x in range(n[1])])
+    c = Case(v, h, nt, nb, vmax, "cross", 4, src=srcs[0], rec=rec, f0=f0)
+    st, stt = c.setup(), Case(vt, h, nt, nb, vmax, "cross", 4, rec=rec, dt=c.dt).setup()
+    wav64 = P.ricker(f0, nt, c.dt)[:, None]
+    dobs = [W.forward(stt, nt, s, wav64, rec, threads=8)[0] for s in srcs]
+    J_o, g_o = 0.0, np.zeros(n)
+    for s, d in zip(srcs, dobs):
+        r = W.forward(st, nt, s, wav64, rec, threads=8)[0] - d
+        J_o += 0.5 * float(np.sum(r ** 2))
+        g_o += W.gradient(st, nt, s, wav64, rec, r, threads=8)[0]
+    dev = torch.device("cuda")
+    plan = c.plan()
+    m = torch.from_numpy(m32).to(dev)
+    wav = torch.from_numpy(F.fd_ricker(f0, c.dt, nt)[:, None].copy()).to(dev)
+    run = gpu_shot_fn(plan, m, [plan.linear_index(s) for s in srcs], [wav] * 3,
+                      plan.linear_index(rec), [torch.from_numpy(d.astype(np.float32)).to(dev) for d in dobs],
+                      k=16)
+    J, g = misfit_and_gradient(m, 3, run)
+    assert abs(J - J_o) < 1e-4 * J_o
+    assert rel_l2(g.cpu().numpy(), g_o) < 1e-4

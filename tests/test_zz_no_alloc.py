@@ -55,3 +55,24 @@ def test_noalloc_rejects_problems_larger_than_the_static_scratch():
         F.fd_forward_noalloc(plan, 0, np.array([0]), 0, np.array([0]), 0)
     assert e.value.code == F.FD_ERR_NOMEM
     assert "static scratch" in F.last_error()
+
+
+def test_noalloc_device_status_is_readable():
+    """A model faster than the plan's vmax is recorded in the status word in the
+    static array, which fd_status_read_noalloc reads and clears; a clean call
+    then reads FD_OK."""
+    import torch
+    import paper_2606_04882_gb300 as F
+    vel = np.full((40, 50), 2000.0, np.float32)
+    c = Case(vel, 10.0, 40, 4, 2500.0, "cross", 4, rec=[[2, 7]])
+    plan = c.plan()
+    dev = torch.device("cuda")
+    wav = torch.from_numpy(c.wavelet32()).to(dev)
+    tr = torch.zeros((c.nt, 1), device=dev)
+    fast = torch.full((40, 50), 2600.0, device=dev)
+    F.fd_forward_noalloc(plan, fast, plan.linear_index(c.src), wav, plan.linear_index(c.rec), tr)
+    assert F.fd_status_read_noalloc(plan) == F.FD_ERR_UNSTABLE
+    assert "vmax" in F.last_error()
+    F.fd_forward_noalloc(plan, torch.from_numpy(vel).to(dev), plan.linear_index(c.src), wav,
+                         plan.linear_index(c.rec), tr)
+    assert F.fd_status_read_noalloc(plan) == F.FD_OK
