@@ -130,6 +130,25 @@ int fd_weights(const fd_stencil_desc *desc, int cap, int *n_orbits,
 int fd_cfl_limit(const fd_stencil_desc *desc, double *courant_max);
 
 /*
+ * fd_weights_conditioning - how well the system fd_weights solves determines
+ * the weights (Section 4.2 names the ill-posed shapes; the LS schemes are
+ * solved as minimum-norm least squares):
+ *   cond        out: sigma_max / sigma_min of the system's matrix (HUGE_VAL when
+ *               a singular value is zero).  LS schemes: the quadrature-weighted
+ *               design matrix of Sections 3.3.3 / 3.4.3 (one column per
+ *               non-centre orbit); DispTE / theta schemes: the moment or polar
+ *               system; SpatTE: the Taylor system of the axis orbits
+ *   rank        out: LS: singular values above 1e-10 sigma_max (those the
+ *               solution keeps); other schemes: the number of independent
+ *               equations
+ *   n_unknowns  out: number of unknowns (columns)
+ * A rank below n_unknowns means the minimum-norm choice, not the equations,
+ * fixes part of the weights.  HOST, FP64.  Errors: as fd_weights.
+ */
+int fd_weights_conditioning(const fd_stencil_desc *desc, double *cond, int *rank,
+                            int *n_unknowns);
+
+/*
  * fd_ricker - Ricker wavelet s(t^n), t^n = n dt, n = 0..nt-1, with peak
  * frequency f0 and delay 1/f0 (the source named in Section 3.1):
  * s(t) = (1 - 2 pi^2 f0^2 (t - 1/f0)^2) exp(-pi^2 f0^2 (t - 1/f0)^2).

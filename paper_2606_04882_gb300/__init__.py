@@ -78,6 +78,7 @@ _SIGS = {
     "fd_cwt_gamma": (_I, [_P, _P, _I, _I, _I, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fd_weights": (_I, [_P, _I, _P, _P, _P, _P]),
     "fd_cfl_limit": (_I, [_P, _P]),
+    "fd_weights_conditioning": (_I, [_P, _P, _P, _P]),
     "fd_ricker": (_I, [_D, _D, _I, _P]),
     "fd_plan_create": (_I, [_P, _P, _P]),
     "fd_plan_destroy": (None, [_P]),
@@ -160,6 +161,14 @@ def fd_cfl_limit(desc: fd_stencil_desc) -> float:
     c = ctypes.c_double(0.0)
     _check(lib().fd_cfl_limit(ctypes.byref(desc), ctypes.byref(c)))
     return c.value
+
+
+def fd_weights_conditioning(desc: fd_stencil_desc):
+    """(condition number, numerical rank, unknowns) of the weight system."""
+    c, r, n = ctypes.c_double(0.0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().fd_weights_conditioning(ctypes.byref(desc), ctypes.byref(c), ctypes.byref(r),
+                                         ctypes.byref(n)))
+    return c.value, r.value, n.value
 
 
 def fd_ricker(f0: float, dt: float, nt: int) -> np.ndarray:

@@ -13,6 +13,7 @@
 // on every host); least-squares schemes assemble the quadrature design matrix
 // and take the truncated minimum-norm solution from a one-sided Jacobi SVD.
 #include <algorithm>
+#include <functional>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -370,12 +371,12 @@ double taylor_cos(double x, int M)
     return s;
 }
 
-// One-sided Jacobi SVD of A (m x n, column-major in `a`): returns singular
-// values and V; U Sigma = A V.  Then x = V Sigma^+ U^T b with the cutoff.
-bool jacobi_lstsq(std::vector<double> a, int m, int n, const std::vector<double> &b,
-                  double rcond, std::vector<double> &x)
+// One-sided Jacobi SVD of A (m x n, column-major in `a`): rotates the columns
+// until they are mutually orthogonal, so that afterwards column j of `a` is
+// sigma_j u_j and A V = U Sigma with V (n x n, column-major) the rotations.
+void jacobi_orthogonalise(std::vector<double> &a, int m, int n, std::vector<double> &V)
 {
-    std::vector<double> V((size_t)n * n, 0.0);
+    V.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
     auto col = [&](int j) { return &a[(size_t)j * m]; };
     for (int sweep = 0; sweep < 60; ++sweep) {
@@ -406,28 +407,45 @@ bool jacobi_lstsq(std::vector<double> a, int m, int n, const std::vector<double>
             }
         if (off < 1e-15) break;
     }
+}
+
+std::vector<double> column_norms(const std::vector<double> &a, int m, int n)
+{
     std::vector<double> sig(n);
-    double smax = 0.0;
     for (int j = 0; j < n; ++j) {
         double s = 0.0;
-        for (int i = 0; i < m; ++i) s += col(j)[i] * col(j)[i];
+        for (int i = 0; i < m; ++i) s += a[(size_t)j * m + i] * a[(size_t)j * m + i];
         sig[j] = std::sqrt(s);
-        smax = std::max(smax, sig[j]);
     }
+    return sig;
+}
+
+// Minimum-norm least squares through the SVD: x = V Sigma^+ U^T b, singular
+// values at or below rcond * sigma_max dropped.
+bool jacobi_lstsq(std::vector<double> a, int m, int n, const std::vector<double> &b,
+                  double rcond, std::vector<double> &x)
+{
+    std::vector<double> V;
+    jacobi_orthogonalise(a, m, n, V);
+    const std::vector<double> sig = column_norms(a, m, n);
+    const double smax = *std::max_element(sig.begin(), sig.end());
     if (smax == 0.0) return false;
     x.assign(n, 0.0);
     for (int j = 0; j < n; ++j) {
         if (sig[j] <= rcond * smax) continue;
         double utb = 0.0;
-        for (int i = 0; i < m; ++i) utb += col(j)[i] * b[i];
+        for (int i = 0; i < m; ++i) utb += a[(size_t)j * m + i] * b[i];
         const double coef = utb / (sig[j] * sig[j]);   // u_j = col_j / sigma_j
         for (int k = 0; k < n; ++k) x[k] += V[(size_t)j * n + k] * coef;
     }
     return true;
 }
 
-int ls_weights(int dim, const std::vector<Orbit> &orbs, int M, int scheme, int basis, double C,
-               double band, std::vector<double> &w)
+// Weighted design matrix of the LS schemes (column-major, m rows), its
+// right-hand side and the orbits of its columns (every non-centre orbit).
+void ls_design(int dim, const std::vector<Orbit> &orbs, int M, int scheme, int basis, double C,
+               double band, std::vector<double> &A, int &m, int &n, std::vector<double> &rhs,
+               std::vector<int> &cols)
 {
     if (basis == FD_LS_PAPER) basis = scheme == FD_SPECLS ? FD_LS_TAYLOR : FD_LS_COSINE;
     const double b = band > 0 ? band : kPi / 2;
@@ -455,12 +473,13 @@ int ls_weights(int dim, const std::vector<Orbit> &orbs, int M, int scheme, int b
                 dw.push_back(8.0 * wm[i] * wp[j]);
             }
     }
-    std::vector<int> cols;
+    cols.clear();
     for (size_t k = 0; k < orbs.size(); ++k)
         if (orbs[k].key[0] || orbs[k].key[1] || orbs[k].key[2]) cols.push_back((int)k);
-    const int n = (int)cols.size();
-    const int m = (int)(xb.size() * dirs.size());
-    std::vector<double> A((size_t)m * n), rhs(m);
+    n = (int)cols.size();
+    m = (int)(xb.size() * dirs.size());
+    A.assign((size_t)m * n, 0.0);
+    rhs.assign(m, 0.0);
     int row = 0;
     for (size_t ib = 0; ib < xb.size(); ++ib)
         for (size_t id = 0; id < dirs.size(); ++id, ++row) {
@@ -480,6 +499,15 @@ int ls_weights(int dim, const std::vector<Orbit> &orbs, int M, int scheme, int b
             }
             rhs[row] = (basis == FD_LS_COSINE ? 1.0 : target) * sw;
         }
+}
+
+int ls_weights(int dim, const std::vector<Orbit> &orbs, int M, int scheme, int basis, double C,
+               double band, std::vector<double> &w)
+{
+    std::vector<double> A, rhs;
+    std::vector<int> cols;
+    int m = 0, n = 0;
+    ls_design(dim, orbs, M, scheme, basis, C, band, A, m, n, rhs, cols);
     std::vector<double> x;
     if (!jacobi_lstsq(A, m, n, rhs, kLsRcond, x)) return FD_ERR_SINGULAR;
     w.assign(orbs.size(), 0.0);
@@ -683,6 +711,75 @@ extern "C" int fd_cfl_limit(const fd_stencil_desc *desc, double *courant_max)
     int st = compute_weights(desc, keys, m, w, nullptr, nullptr);
     if (st) return st;
     return compute_cfl(desc, w, courant_max);
+}
+
+namespace {
+
+// The min(m, n) largest singular values of a moment or theta system (dd
+// entries rounded to double): an under-determined system (m < n) has no more
+// than m non-zero ones.
+std::vector<double> system_singular_values(const Mat &M)
+{
+    const int m = (int)M.size(), n = m ? (int)M[0].size() : 0;
+    std::vector<double> a((size_t)m * n), V;
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) a[(size_t)j * m + i] = M[i][j].hi + M[i][j].lo;
+    jacobi_orthogonalise(a, m, n, V);
+    std::vector<double> sig = column_norms(a, m, n);
+    std::sort(sig.begin(), sig.end(), std::greater<double>());
+    sig.resize(std::min(m, n));
+    return sig;
+}
+
+}  // namespace
+
+extern "C" int fd_weights_conditioning(const fd_stencil_desc *d, double *cond, int *rank,
+                                       int *n_unknowns)
+{
+    clear_error();
+    if (!cond || !rank || !n_unknowns) return set_error(FD_ERR_ARG, "NULL output");
+    int st = check_desc(d);
+    if (st) return st;
+    const int dim = d->dim, M = d->M;
+    auto orbs = build_orbits(dim, d->shape, M, d->N);
+    auto is_axis = [](const std::array<int, 3> &k) { return k[1] == 0; };
+    std::vector<double> sig;
+    int r = 0, n_unk = 0;
+    if (d->scheme == FD_SPECLS || d->scheme == FD_DISPLS) {
+        std::vector<double> A, rhs;
+        std::vector<int> cols;
+        int m = 0, n = 0;
+        ls_design(dim, orbs, M, d->scheme, d->ls_basis, d->courant, d->band, A, m, n, rhs, cols);
+        std::vector<double> V;
+        jacobi_orthogonalise(A, m, n, V);
+        sig = column_norms(A, m, n);
+        n_unk = n;
+        const double smax = sig.empty() ? 0.0 : *std::max_element(sig.begin(), sig.end());
+        for (double v : sig) r += v > kLsRcond * smax;
+    } else {
+        std::vector<Orbit> sub;
+        for (auto &o : orbs)
+            if (d->scheme == FD_DISPTE || d->scheme == FD_DISPTE_THETA || is_axis(o.key)) sub.push_back(o);
+        Mat A;
+        std::vector<dd> b;
+        if (d->scheme == FD_SPECTE_THETA || d->scheme == FD_DISPTE_THETA) {
+            if (dim != 2) return set_error(FD_ERR_UNSUPPORTED, "theta schemes are defined for 2D only");
+            theta_system(sub, M, d->scheme == FD_DISPTE_THETA ? d->courant : 0.0, d->theta, A, b);
+        } else if (d->scheme == FD_DISPTE) {
+            moment_system(dim, sub, M, d->courant, mixed_order(d->shape, M, d->N), A, b);
+        } else {   // SpatTE: the Taylor system of the axis orbits
+            moment_system(dim, sub, M, 0.0, 1, A, b);
+        }
+        sig = system_singular_values(A);
+        r = (int)independent_rows(A).size();
+        n_unk = A.empty() ? 0 : (int)A[0].size();
+    }
+    const double smax = sig.empty() ? 0.0 : *std::max_element(sig.begin(), sig.end());
+    const double smin = sig.empty() ? 0.0 : *std::min_element(sig.begin(), sig.end());
+    *cond = smin > 0.0 ? smax / smin : HUGE_VAL;
+    *rank = r;
+    *n_unknowns = n_unk;
+    return FD_OK;
 }
 
 extern "C" int fd_ricker(double f0, double dt, int nt, float *out)

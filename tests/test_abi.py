@@ -164,3 +164,37 @@ def test_symbol_positive_stencil_is_rejected(M, N):
         assert e.value.code == F.FD_ERR_UNSTABLE
     dc = F.stencil_desc(2, "cross", M)
     F.Plan((40, 40), h, 0.5 * F.fd_cfl_limit(dc) * h / v, 10, 5, v, dc)
+
+
+def test_weights_conditioning():
+    """fd_weights_conditioning against matrices built here.
+    - SpatTE Cross(M), 2D: the Taylor system in orbit form (Eq. taylor_system),
+      rows r = 0..M, columns (centre, axis orbits m = 1..M): row 0 holds the
+      orbit sizes (1, 4, ..., 4), row r >= 1 holds sum over the orbit of
+      x^(2r) = 2 m^(2r).
+    - DispLS: the design matrix of E_disp(b) on this suite's own quadrature;
+      singular values of a smooth Gram operator barely depend on the rule.
+    - Square(8) DispLS keeps fewer singular values than unknowns (the
+      minimum-norm cutoff fixes part of the weights), and the under-determined
+      DispTE square reports its equation count as rank."""
+    from test_oracle_weights import _displs_design
+    for M in (1, 2, 4, 8):
+        A = np.zeros((M + 1, M + 1))
+        A[0] = [1] + [4] * M
+        for r in range(1, M + 1):
+            A[r, 1:] = [2.0 * m ** (2 * r) for m in range(1, M + 1)]
+        c, r, n = F.fd_weights_conditioning(F.stencil_desc(2, "cross", M))
+        assert (r, n) == (M + 1, M + 1)
+        # at M = 8 (condition ~2e15) two double-precision SVDs agree to ~1 %
+        assert abs(c / np.linalg.cond(A) - 1) < (1e-6 if M <= 4 else 2e-2)
+    for shape, M in (("cross", 4), ("rhombus", 4), ("square", 4)):
+        d = F.stencil_desc(2, shape, M, 0, "displs", courant=0.3)
+        c, r, n = F.fd_weights_conditioning(d)
+        keys = [k for k in S.weights(2, shape, M, 0, "displs", C=0.3) if any(k)]
+        A, W = _displs_design(2, keys, 0.3, np.pi / 2, n_beta=48, n_dir=24)
+        assert (r, n) == (len(keys), len(keys))
+        assert abs(c / np.linalg.cond(A * np.sqrt(W)[:, None]) - 1) < 0.05, (shape, c)
+    c, r, n = F.fd_weights_conditioning(F.stencil_desc(2, "square", 8, 0, "displs", courant=0.3))
+    assert n == 44 and r < n and c > 1e12
+    c, r, n = F.fd_weights_conditioning(F.stencil_desc(2, "square", 3, 0, "dispte", courant=0.3))
+    assert n == 10 and r < n and np.isfinite(c)
