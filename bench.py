@@ -531,6 +531,7 @@ def run_other(args):
     roof = {"bound": "hbm", "achieved": kernels[dom]["achieved_gbs"], "peak": peak, "unit": "GB/s",
             "frac": kernels[dom]["frac"], "traffic": None, "kernel": kernels[dom]["run"],
             "bytes_per_point": bpp, "peak_source": peak_kind}
+    compare = batched_vs_single(args, dev, stream, shots) if args.workload == "batched" else None
     if args.workload == "2d":
         roof["note"] = "fields (4.7 MB) are L2-resident: the HBM fraction is nominal"
     if args.workload == "fwi":
@@ -545,10 +546,80 @@ def run_other(args):
            "e2e": None, "roofline": roof, "kernels": kernels, "cpu_baseline": None,
            "clocks": clocks,
            "gpu_launches": args.steps * sum(j[4] for j in jobs)}
+    if compare is not None:
+        out["batched_vs_single_shot"] = compare
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def batched_vs_single(args, dev, stream, shots, grad_shots=8, k=GRAD_K):
+    """The batched forward of all shots against one fd_forward call per shot on
+    the same inputs, and the batched gradient of the first `grad_shots` shots
+    against one fd_adjoint_gradient call per shot (checkpoints every k steps,
+    seeded residuals).  Same arithmetic, so the traces and gradients are
+    checked to be bitwise equal; times are CUDA events, best of `args.steps`."""
+    import torch
+    import paper_2606_04882_gb300 as F
+
+    def best(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(args.steps, 1)):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return min(ts)
+
+    nt = shots[0]["plan"].nt
+    pts = [int(np.prod(d["plan"].padded_shape)) for d in shots]
+    ws = F.workspace(F.batched_workspace_size(shots), dev)
+    ms_b = best(lambda: F.fd_forward_batched(shots, ws))
+    tr_b = [d["traces"].clone() for d in shots]
+    wss = [F.workspace(d["plan"].forward_workspace_size(len(d["src_idx"]), len(d["rec_idx"])), dev)
+           for d in shots]
+
+    def single():
+        for d, w in zip(shots, wss):
+            F.fd_forward(d["plan"], d["model"], d["src_idx"], d["wavelet"], d["rec_idx"], d["traces"], w)
+    ms_s = best(single)
+    same_fwd = all(torch.equal(a, d["traces"]) for a, d in zip(tr_b, shots))
+    del ws, wss
+    gs = []
+    for i, d in enumerate(shots[:grad_shots]):
+        g = torch.Generator(dev).manual_seed(100 + i)
+        gs.append(dict(d, resid=torch.randn(d["traces"].shape, device=dev, generator=g),
+                       grad=torch.empty_like(d["model"])))
+    wsg = F.workspace(F.batched_gradient_workspace_size(gs, k), dev)
+    gms_b = best(lambda: F.fd_adjoint_gradient_batched(gs, k, wsg))
+    g_b = [d["grad"].clone() for d in gs]
+    del wsg
+    wsgs = [F.workspace(d["plan"].gradient_workspace_size(len(d["src_idx"]), len(d["rec_idx"]), k), dev)
+            for d in gs]
+
+    def single_grad():
+        for d, w in zip(gs, wsgs):
+            F.fd_adjoint_gradient(d["plan"], d["model"], d["src_idx"], d["wavelet"], d["rec_idx"],
+                                  d["resid"], k, d["grad"], w)
+    gms_s = best(single_grad)
+    same_grad = all(torch.equal(a, d["grad"]) for a, d in zip(g_b, gs))
+    work = sum(pts) * nt
+    gwork = sum(pts[:len(gs)]) * nt
+    return {"forward": {"shots": len(shots), "batched_gpts": work / (ms_b * 1e-3) / 1e9,
+                        "single_shot_gpts": work / (ms_s * 1e-3) / 1e9, "batched_ms": ms_b,
+                        "single_shot_ms": ms_s, "speedup": ms_s / ms_b, "bitwise_equal": same_fwd},
+            "gradient": {"shots": len(gs), "ckpt_every": k,
+                         "batched_gpts": gwork / (gms_b * 1e-3) / 1e9,
+                         "single_shot_gpts": gwork / (gms_s * 1e-3) / 1e9, "batched_ms": gms_b,
+                         "single_shot_ms": gms_s, "speedup": gms_s / gms_b,
+                         "bitwise_equal": same_grad},
+            "note": "gradient points per second count padded points x time steps of the "
+                    "gradient (its three sweeps)"}
 
 
 def run_metrics(args):

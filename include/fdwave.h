@@ -216,6 +216,21 @@ int fd_plan_autotune(fd_plan *plan, int model_kind, const float *model_d, void *
                      size_t ws_bytes, void *stream);
 
 /*
+ * fd_plan_variants / fd_plan_set_variant - the kernel variants built for the
+ * plan's stencil, and choosing one by hand instead of the default or
+ * fd_plan_autotune (the paper has no counterpart: these are schedules of the
+ * same arithmetic, and results do not depend on the variant).
+ *   2D: rows per thread R (1, 2 or 4) of the 64 x 16R tile.
+ *   3D: rows TY (8 or 16) of the 64 x TY column a CTA marches in z.
+ * fd_plan_variants writes up to cap entries and sets n to the number built
+ * (0 for the generic 2D kernel).  fd_plan_set_variant takes one of them and
+ * a z-chunk in planes per CTA (3D; 0 lets the cost model choose).
+ * Errors: FD_ERR_ARG, FD_ERR_UNSUPPORTED (variant not built).
+ */
+int fd_plan_variants(const fd_plan *plan, int cap, int *n, int *variants);
+int fd_plan_set_variant(fd_plan *plan, int variant, int z_chunk);
+
+/*
  * fd_forward_workspace_size - bytes of device workspace fd_forward needs for
  * nsrc sources and nrec receivers (three padded field buffers, tile-bucketed
  * source/receiver tables, the status word).  The tables are sized for the
@@ -316,6 +331,41 @@ typedef struct {
 int fd_forward_batched_workspace_size(int nshots, const fd_shot *shots, size_t *bytes);
 int fd_forward_batched(int nshots, const fd_shot *shots, void *ws_d, size_t ws_bytes,
                        void *stream);
+
+/*
+ * Batched gradients (the paper has no counterpart; its FWI outlook sums the
+ * gradients of many shots): the checkpointed adjoint gradient of
+ * fd_adjoint_gradient for several shots in one call, each shot with its own
+ * plan (grids may differ; stencil, dt and nt are shared), model, sources,
+ * receivers, residuals and gradient output.  For 2D cross stencils with
+ * M = 2, 4 or 8 every time step of each sweep is one launch of persistent
+ * CTAs over the tiles of every shot; other batches run the shots one after
+ * another.  Each shot's gradient (and traces) are bit for bit those of
+ * fd_adjoint_gradient with the same ckpt_every.  Workspace: every shot's
+ * gradient workspace plus the batch's tables.  Device status: the first
+ * shot's status word (fd_status_read with the first plan and ws_d).
+ * Errors: FD_ERR_ARG (shots that differ in dim, stencil, dt or nt, missing
+ * outputs), FD_ERR_NOMEM, FD_ERR_CUDA.
+ */
+typedef struct {
+    const fd_plan *plan;      /* plan of this shot's grid (shared stencil/dt/nt) */
+    int32_t model_kind;
+    int32_t nsrc;
+    int32_t nrec;
+    int32_t reserved;
+    const float *model_d;
+    const int64_t *src_idx;   /* HOST */
+    const float *wavelet_d;   /* [nt][nsrc] */
+    const int64_t *rec_idx;   /* HOST */
+    const float *resid_d;     /* [nt][nrec] dJ/dtrace */
+    float *grad_d;            /* out: physical dJ/dm of this shot */
+    float *traces_d;          /* optional out [nt][nrec] of the forward sweep (NULL: none) */
+} fd_grad_shot;
+
+int fd_adjoint_gradient_batched_workspace_size(int nshots, const fd_grad_shot *shots,
+                                               int ckpt_every, size_t *bytes);
+int fd_adjoint_gradient_batched(int nshots, const fd_grad_shot *shots, int ckpt_every,
+                                void *ws_d, size_t ws_bytes, void *stream);
 
 /*
  * fd_forward_noalloc - fd_forward for callers that cannot allocate device

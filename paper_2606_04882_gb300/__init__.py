@@ -64,6 +64,15 @@ class fd_shot(ctypes.Structure):
                 ("traces_d", ctypes.c_void_p)]
 
 
+class fd_grad_shot(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("model_kind", ctypes.c_int32),
+                ("nsrc", ctypes.c_int32), ("nrec", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("model_d", ctypes.c_void_p), ("src_idx", ctypes.c_void_p),
+                ("wavelet_d", ctypes.c_void_p), ("rec_idx", ctypes.c_void_p),
+                ("resid_d", ctypes.c_void_p), ("grad_d", ctypes.c_void_p),
+                ("traces_d", ctypes.c_void_p)]
+
+
 class FdError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("fdwave error %d: %s" % (code, msg))
@@ -84,6 +93,8 @@ _SIGS = {
     "fd_plan_destroy": (None, [_P]),
     "fd_plan_get_info": (_I, [_P, _P]),
     "fd_plan_autotune": (_I, [_P, _I, _P, _P, _SZ, _P]),
+    "fd_plan_variants": (_I, [_P, _I, _P, _P]),
+    "fd_plan_set_variant": (_I, [_P, _I, _I]),
     "fd_forward_workspace_size": (_I, [_P, _I, _I, _P]),
     "fd_forward": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
     "fd_status_read": (_I, [_P, _P, _P]),
@@ -92,6 +103,8 @@ _SIGS = {
     "fd_forward_batched_workspace_size": (_I, [_I, _P, _P]),
     "fd_forward_batched": (_I, [_I, _P, _P, _SZ, _P]),
     "fd_forward_noalloc": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P]),
+    "fd_adjoint_gradient_batched_workspace_size": (_I, [_I, _P, _I, _P]),
+    "fd_adjoint_gradient_batched": (_I, [_I, _P, _I, _P, _SZ, _P]),
     "fd_status_read_noalloc": (_I, [_P, _P]),
     "fd_last_error": (ctypes.c_char_p, []),
     "fd_version": (ctypes.c_char_p, []),
@@ -233,6 +246,18 @@ class Plan:
         ws = workspace(self.forward_workspace_size(0, 0) + 4096, model.device)
         _check(lib().fd_plan_autotune(self.ptr, model_kind, _addr(model), _addr(ws), ws.numel(),
                                       _stream_ptr(stream)))
+        return self.info()
+
+    def variants(self):
+        """Kernel variants built for this plan's stencil (fd_plan_variants)."""
+        n = ctypes.c_int(0)
+        buf = (ctypes.c_int * 16)()
+        _check(lib().fd_plan_variants(self.ptr, 16, ctypes.byref(n), buf))
+        return list(buf[:n.value])
+
+    def set_variant(self, variant: int, z_chunk: int = 0):
+        """fd_plan_set_variant; returns the plan info."""
+        _check(lib().fd_plan_set_variant(self.ptr, variant, z_chunk))
         return self.info()
 
     def forward_workspace_size(self, nsrc: int, nrec: int) -> int:
@@ -399,6 +424,36 @@ def batched_workspace_size(shots: Sequence[dict]) -> int:
     b = ctypes.c_size_t(0)
     _check(lib().fd_forward_batched_workspace_size(len(shots), arr, ctypes.byref(b)))
     return b.value
+
+
+def _grad_shots(shots: Sequence[dict]):
+    arr = (fd_grad_shot * len(shots))()
+    keep = []
+    for i, s in enumerate(shots):
+        si = np.ascontiguousarray(s.get("src_idx", np.zeros(0)), np.int64)
+        ri = np.ascontiguousarray(s.get("rec_idx", np.zeros(0)), np.int64)
+        keep += [si, ri]
+        arr[i] = fd_grad_shot(s["plan"].ptr.value, s.get("model_kind", FD_MODEL_VELOCITY), len(si),
+                              len(ri), 0, _addr(s.get("model")), si.ctypes.data if len(si) else None,
+                              _addr(s.get("wavelet")), ri.ctypes.data if len(ri) else None,
+                              _addr(s.get("resid")), _addr(s.get("grad")), _addr(s.get("traces")))
+    return arr, keep
+
+
+def batched_gradient_workspace_size(shots: Sequence[dict], k: int) -> int:
+    arr, _ = _grad_shots(shots)
+    b = ctypes.c_size_t(0)
+    _check(lib().fd_adjoint_gradient_batched_workspace_size(len(shots), arr, k, ctypes.byref(b)))
+    return b.value
+
+
+def fd_adjoint_gradient_batched(shots: Sequence[dict], k: int, ws, stream=None):
+    """shots: dicts with plan, model, src_idx, wavelet, rec_idx, resid, grad
+    (and optional traces, model_kind); each shot's gradient is written to its
+    grad tensor."""
+    arr, keep = _grad_shots(shots)
+    _check(lib().fd_adjoint_gradient_batched(len(shots), arr, k, _addr(ws), ws.numel(),
+                                             _stream_ptr(stream)))
 
 
 # ----------------------------------------------------------------------------

@@ -106,6 +106,11 @@ struct ShotInfo {
     int64_t phys_lo[3], phys_hi[3];
     float gcoef;
     int tiles_x, inj_ncol, smp_ncol;
+    // gradient sweeps of a batch: D of step n of the current segment at
+    // dseg + (n - segment start) * field, and the accumulator g
+    float *dseg;
+    float *gacc;
+    int64_t field;             // floats per field buffer
 };
 
 struct alignas(128) ShotDesc {
@@ -137,7 +142,9 @@ struct BatchParams {
     const PtEntry *ext;
     int roles[4];
     int ntiles;                // tiles of all shots
-    int step;                  // time step n (field parity and series row)
+    int step;                  // time step n (series row)
+    int parity;                // field buffer (0 or 1 of the descriptor) holding the stencil input
+    int seg;                   // gradient sweeps: index of this step's D in its segment
     int check;                 // 1: check this step's outputs for growth (kStatusBlowup)
     int *status;
     float w[kWDim * kWDim];
@@ -173,12 +180,16 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
 // Tuning candidates: rows per thread (2D) / y tile (3D) with a kernel.
 int variants_2d(int shape, int M, int *r_out, int cap);
 int variants_3d(int shape, int M, int *ty_out, int cap);
+constexpr int kMaxVariants = 8;
+
 cudaError_t launch_step2d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
 cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
+int occupancy_3d(const Variant &v);
 int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v);
 int persist2d_grid(const Variant &v, int ntiles);
 cudaError_t launch_persist2d(const Variant &v, const PersistParams &pp, int grid, cudaStream_t s);
-cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s);
+cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s,
+                             int mode = kModeForward);
 // Two-step batched kernel (u^{n+1} and u^{n+2} per pass): geometry of its
 // boxes for cross stencils with M <= 4 (FD_ERR_UNSUPPORTED otherwise).
 struct Batch2Geo {

@@ -240,9 +240,7 @@ int ensure_tuned(fd_plan *p)
         int dev = 0, nsm = 152, occ = 1;
         FDW_CK(cudaGetDevice(&dev));
         FDW_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        int smem_sm = 0;
-        FDW_CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-        occ = std::max(1, std::min((int)(smem_sm / (p->var.smem + 2048)), 2048 / p->var.threads));
+        occ = std::max(1, occupancy_3d(p->var));
         const int64_t slots = (int64_t)nsm * occ;
         const int M = p->st.M;
         double best = 1e300;
@@ -471,9 +469,9 @@ extern "C" int fd_plan_create(const fd_problem *prob, const fd_stencil_desc *ste
     p->ntiles = p->tiles_x * p->tiles_y;
     p->max_tiles = p->ntiles;
     {
-        int prefs[4];
-        const int np = pr.dim == 2 ? variants_2d(p->shape_eff, M, prefs, 4)
-                                   : variants_3d(p->shape_eff, M, prefs, 4);
+        int prefs[kMaxVariants];
+        const int np = pr.dim == 2 ? variants_2d(p->shape_eff, M, prefs, kMaxVariants)
+                                   : variants_3d(p->shape_eff, M, prefs, kMaxVariants);
         for (int i = 0; i < np; ++i) {
             Variant v;
             if (pr.dim == 2 ? select_variant_2d(p->shape_eff, M, stencil->N, padx, padz, &v, prefs[i])
@@ -593,9 +591,9 @@ extern "C" int fd_plan_autotune(fd_plan *p, int model_kind, const float *model, 
     if (it != g_tune.end()) return apply_choice(p, it->second);
     if (p->var.generic) return FD_OK;   // a single kernel: nothing to choose
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    int prefs[4];
-    const int np = p->prob.dim == 2 ? variants_2d(p->shape_eff, p->st.M, prefs, 4)
-                                    : variants_3d(p->shape_eff, p->st.M, prefs, 4);
+    int prefs[kMaxVariants];
+    const int np = p->prob.dim == 2 ? variants_2d(p->shape_eff, p->st.M, prefs, kMaxVariants)
+                                    : variants_3d(p->shape_eff, p->st.M, prefs, kMaxVariants);
     std::vector<TuneChoice> cands;
     for (int i = 0; i < np; ++i) {
         if (p->prob.dim == 2) {
@@ -662,6 +660,10 @@ extern "C" int fd_plan_autotune(fd_plan *p, int model_kind, const float *model, 
         float t64 = 0.f, t16 = 0.f;
         if ((st = timed(q, 64, t64)) || (st = timed(q, 16, t16))) break;
         const float ms = (t64 - t16) / 48.f;
+        if (const char *vb = getenv("FDWAVE_TUNE_VERBOSE"))
+            if (vb[0] == '1')
+                fprintf(stderr, "fdwave tune %s: tile %d z-chunk %d: %.4f ms per step\n",
+                        key.c_str(), c.pref, c.zchunk, ms);
         // a later candidate must win by 2 %: the first of each tile shape is
         // the cost model's z-chunk, and near-ties are timing noise
         if (ms < 0.98f * best) {
@@ -675,6 +677,41 @@ extern "C" int fd_plan_autotune(fd_plan *p, int model_kind, const float *model, 
     g_tune[key] = bestc;
     tune_file_store(key, bestc);
     return apply_choice(p, bestc);
+}
+
+extern "C" int fd_plan_variants(const fd_plan *p, int cap, int *n, int *variants)
+{
+    clear_error();
+    if (!p || !n || cap < 0 || (cap > 0 && !variants)) return set_error(FD_ERR_ARG, "bad argument");
+    int prefs[kMaxVariants];
+    const int np = p->var.generic ? 0
+                 : p->prob.dim == 2 ? variants_2d(p->shape_eff, p->st.M, prefs, kMaxVariants)
+                                    : variants_3d(p->shape_eff, p->st.M, prefs, kMaxVariants);
+    *n = np;
+    for (int i = 0; i < np && i < cap; ++i) variants[i] = prefs[i];
+    return FD_OK;
+}
+
+extern "C" int fd_plan_set_variant(fd_plan *p, int variant, int z_chunk)
+{
+    clear_error();
+    if (!p || z_chunk < 0) return set_error(FD_ERR_ARG, "bad argument");
+    if (p->var.generic) return set_error(FD_ERR_UNSUPPORTED, "the generic 2D kernel has no variants");
+    int prefs[kMaxVariants];
+    const int np = p->prob.dim == 2 ? variants_2d(p->shape_eff, p->st.M, prefs, kMaxVariants)
+                                    : variants_3d(p->shape_eff, p->st.M, prefs, kMaxVariants);
+    if (std::find(prefs, prefs + np, variant) == prefs + np)
+        return set_error(FD_ERR_UNSUPPORTED, "variant %d is not built for this stencil", variant);
+    if (p->prob.dim == 2 && z_chunk) return set_error(FD_ERR_ARG, "2D plans have no z-chunk");
+    TuneChoice c{variant, z_chunk};
+    if (p->prob.dim == 3 && z_chunk == 0) {
+        Variant v;
+        int st = select_variant_3d(p->shape_eff, p->st.M, p->st.N, p->pad[2], p->pad[1], p->pad[0], &v, variant);
+        if (st) return set_error(st, "variant %d is not available", variant);
+        apply_variant(p, v);
+        return ensure_tuned(p);     // cost-model z-chunk
+    }
+    return apply_choice(p, c);
 }
 
 extern "C" int fd_plan_get_info(const fd_plan *p, fd_plan_info *info)
@@ -1282,6 +1319,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
             d.info.phys_lo[2] = p->prob.nb; d.info.phys_hi[2] = p->prob.nb + p->prob.n[0] - 1;
             d.info.gcoef = p->gcoef;
             d.info.tiles_x = geo[i].tiles_x;
+            d.info.field = p->field;
             const int32_t *hip = reinterpret_cast<const int32_t *>(T.blob.data() + T.inj_ptr);
             const int32_t *hsp = reinterpret_cast<const int32_t *>(T.blob.data() + T.smp_ptr);
             // sources of each tile's extended region (tile plus the halo whose
@@ -1391,6 +1429,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
             int n = 0, cur = 0, prev = 1;
             if (nt & 1) {
                 bp.step = 0;
+                bp.parity = 0;
                 bp.check = check_step(0, nt);
                 ce = launch_batched2d(bv, bp, ntiles, cs);
                 n = 1; cur = 1; prev = 0;
@@ -1407,6 +1446,7 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         for (int n = 0; n < nt && ce == cudaSuccess && !two; ++n) {
             if (one) {
                 bp.step = n;
+                bp.parity = n & 1;
                 bp.check = check_step(n, nt);
                 ce = launch_batched2d(bv, bp, ntiles, cs);
                 continue;
@@ -1435,5 +1475,283 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         graph_cache_put(key, ge);
     }
     FDW_CK(cudaGraphLaunch(ge, s));
+    return FD_OK;
+}
+
+// ---------------------------- batched gradient ----------------------------
+// The checkpointed adjoint gradient of many shots.  For 2D shots of a cross
+// stencil with M = 2, 4 or 8 every step of each sweep (forward with
+// checkpoints, segment recompute storing D, adjoint with the fused gradient)
+// is one launch of the batched tile kernel over the tiles of every shot; each
+// shot keeps its own buffers, checkpoints, segment and accumulator, so its
+// gradient is bit for bit the one fd_adjoint_gradient gives.  Other batches
+// run the shots one after another.
+
+namespace {
+
+std::vector<fd_shot> as_shots(int nshots, const fd_grad_shot *g)
+{
+    std::vector<fd_shot> v(nshots);
+    for (int i = 0; i < nshots; ++i) {
+        std::memset(&v[i], 0, sizeof v[i]);
+        v[i].plan = g[i].plan;
+        v[i].nsrc = g[i].nsrc;
+        v[i].nrec = g[i].nrec;
+    }
+    return v;
+}
+
+size_t grad_batch_bytes(int nshots, const fd_grad_shot *shots, int k, bool one,
+                        const std::vector<TileGeo> &geo, int64_t *ntiles_out)
+{
+    size_t tot = 0;
+    int64_t ntiles = 0;
+    for (int i = 0; i < nshots; ++i) {
+        const fd_plan *p = shots[i].plan;
+        const int kk = std::min(k, std::max(p->prob.nt, 1));
+        tot += make_layout(p, shots[i].nsrc, shots[i].nrec, true, kk, one ? geo[i].ntiles : -1).total;
+        if (one) ntiles += geo[i].ntiles;
+    }
+    if (one) tot += 2 * up(nshots * sizeof(ShotDesc)) + 3 * up(ntiles * sizeof(TileRec));
+    if (ntiles_out) *ntiles_out = ntiles;
+    return tot;
+}
+
+}  // namespace
+
+extern "C" int fd_adjoint_gradient_batched_workspace_size(int nshots, const fd_grad_shot *shots,
+                                                          int ckpt_every, size_t *bytes)
+{
+    clear_error();
+    if (nshots < 0 || (nshots > 0 && !shots) || !bytes || ckpt_every < 1)
+        return set_error(FD_ERR_ARG, "bad argument");
+    for (int i = 0; i < nshots; ++i)
+        if (!shots[i].plan) return set_error(FD_ERR_ARG, "shot %d has no plan", i);
+    Variant bv;
+    std::vector<TileGeo> geo;
+    std::vector<fd_shot> fs = as_shots(nshots, shots);
+    const bool one = nshots > 0 && batch_geometry(nshots, fs.data(), bv, geo);
+    *bytes = grad_batch_bytes(nshots, shots, ckpt_every, one, geo, nullptr);
+    return FD_OK;
+}
+
+extern "C" int fd_adjoint_gradient_batched(int nshots, const fd_grad_shot *shots, int k, void *ws,
+                                           size_t ws_bytes, void *stream)
+{
+    clear_error();
+    size_t need = 0;
+    int st = fd_adjoint_gradient_batched_workspace_size(nshots, shots, k, &need);
+    if (st) return st;
+    if (!ws || ws_bytes < need) return set_error(FD_ERR_NOMEM, "workspace too small (%zu < %zu)", ws_bytes, need);
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return set_error(FD_ERR_ARG, "workspace must be 256-byte aligned");
+    if (nshots == 0) return FD_OK;
+    const fd_plan *p0 = shots[0].plan;
+    for (int i = 1; i < nshots; ++i) {
+        const fd_plan *q = shots[i].plan;
+        if (q->prob.dim != p0->prob.dim || q->prob.nt != p0->prob.nt || q->prob.dt != p0->prob.dt ||
+            q->st.M != p0->st.M || q->st.shape != p0->st.shape || q->st.scheme != p0->st.scheme ||
+            std::memcmp(q->W, p0->W, sizeof q->W) != 0)
+            return set_error(FD_ERR_ARG, "shot %d: batched shots must share dim, stencil, dt and nt", i);
+    }
+    for (int i = 0; i < nshots; ++i)
+        if (!shots[i].grad_d || (shots[i].nrec > 0 && !shots[i].resid_d))
+            return set_error(FD_ERR_ARG, "shot %d needs a gradient output and residuals", i);
+    Variant bv;
+    std::vector<TileGeo> geo;
+    std::vector<fd_shot> fs = as_shots(nshots, shots);
+    const bool one = batch_geometry(nshots, fs.data(), bv, geo);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *base = reinterpret_cast<char *>(ws);
+    if (!one) {   // shot by shot, each in its slice of the workspace
+        for (int i = 0; i < nshots; ++i) {
+            const fd_grad_shot &g = shots[i];
+            fd_plan *p = const_cast<fd_plan *>(g.plan);
+            const int kk = std::min(k, std::max(p->prob.nt, 1));
+            const size_t b = make_layout(p, g.nsrc, g.nrec, true, kk).total;
+            st = fd_adjoint_gradient(p, g.model_kind, g.model_d, g.nsrc, g.src_idx, g.wavelet_d, g.nrec,
+                                     g.rec_idx, g.resid_d, k, g.grad_d, g.traces_d, nullptr, base, b, stream);
+            if (st) return set_error(st, "shot %d: %s", i, fd_last_error());
+            base += b;
+        }
+        return FD_OK;
+    }
+    const int nt = p0->prob.nt;
+    k = std::min(k, std::max(nt, 1));
+    const int nck = (nt + k - 1) / k;
+    int64_t ntiles_all = 0;
+    size_t shots_bytes = 0;
+    for (int i = 0; i < nshots; ++i) {
+        shots_bytes += make_layout(shots[i].plan, shots[i].nsrc, shots[i].nrec, true, k, geo[i].ntiles).total;
+        ntiles_all += geo[i].ntiles;
+    }
+    char *xd = base + shots_bytes;                      // forward descriptors
+    char *xa = xd + up(nshots * sizeof(ShotDesc));      // adjoint descriptors
+    char *xr = xa + up(nshots * sizeof(ShotDesc));      // tile records: forward | recompute | adjoint
+    const size_t rb = up(ntiles_all * sizeof(TileRec));
+    std::vector<ShotDesc> df(nshots), da(nshots);
+    std::vector<TileRec> rf, rr, ra;
+    struct ShotBufs {
+        float *buf[4];
+        char *ckpt;
+        float *gacc;
+        size_t fb;
+    };
+    std::vector<ShotBufs> sb(nshots);
+    for (int i = 0; i < nshots; ++i) {
+        fd_plan *p = const_cast<fd_plan *>(shots[i].plan);
+        const fd_grad_shot &g = shots[i];
+        const Layout L = make_layout(p, g.nsrc, g.nrec, true, k, geo[i].ntiles);
+        st = check_common(p, g.model_kind, g.model_d, g.nsrc, g.src_idx, g.wavelet_d, g.nrec, g.rec_idx,
+                          base, L.total, L.total);
+        if (st) return set_error(st, "shot %d: %s", i, fd_last_error());
+        if ((st = ensure_tuned(p))) return st;
+        Tables T;
+        if ((st = make_tables(p, g.nsrc, g.src_idx, g.nrec, g.rec_idx, true, T, &geo[i]))) return st;
+        if ((st = upload_tables(p, L, base, T, s))) return st;
+        FDW_CK(cudaMemsetAsync(base + L.status, 0, kAlign, s));
+        const size_t fb = up((size_t)p->field * sizeof(float));
+        ShotBufs &b = sb[i];
+        b.fb = fb;
+        for (int j = 0; j < 4; ++j) {
+            b.buf[j] = reinterpret_cast<float *>(base + L.buf[j]);
+            FDW_CK(cudaMemsetAsync(b.buf[j], 0, fb, s));
+        }
+        b.gacc = reinterpret_cast<float *>(base + L.gacc);
+        FDW_CK(cudaMemsetAsync(b.gacc, 0, fb, s));
+        b.ckpt = base + L.ckpt;
+        if ((st = prep_model(p, L, base, g.model_kind, g.model_d, s))) return st;
+        const float *kap = reinterpret_cast<const float *>(base + L.kappa);
+        float *dseg = reinterpret_cast<float *>(base + L.dseg);
+        auto fill = [&](ShotDesc &d, float *b0, float *b1) -> int {
+            std::memset(&d, 0, sizeof d);
+            Variant keep = p->var;
+            p->var = bv;
+            int r = encode_field_map(p, &d.tmap[0], b0, false);
+            r = r ? r : encode_field_map(p, &d.tmap[1], b1, false);
+            r = r ? r : encode_field_map(p, &d.tile[0], b0, true);
+            r = r ? r : encode_field_map(p, &d.tile[1], b1, true);
+            r = r ? r : encode_field_map(p, &d.ktile, kap, true);
+            p->var = keep;
+            d.info.buf[0] = b0;
+            d.info.buf[1] = b1;
+            d.info.kappa = kap;
+            d.info.nx = p->pad[2];
+            d.info.nz = p->pad[0];
+            d.info.pitch = p->pitch;
+            d.info.phys_lo[0] = p->prob.nb; d.info.phys_hi[0] = p->prob.nb + p->prob.n[2] - 1;
+            d.info.phys_lo[2] = p->prob.nb; d.info.phys_hi[2] = p->prob.nb + p->prob.n[0] - 1;
+            d.info.gcoef = p->gcoef;
+            d.info.tiles_x = geo[i].tiles_x;
+            d.info.dseg = dseg;
+            d.info.field = (int64_t)(fb / sizeof(float));
+            return r;
+        };
+        if (fill(df[i], b.buf[0], b.buf[1]) || fill(da[i], b.buf[2], b.buf[3]))
+            return set_error(FD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+        // forward / recompute: sources in, receivers out; adjoint: residuals in
+        df[i].info.inj = reinterpret_cast<const PtEntry *>(base + L.tab + T.inj);
+        df[i].info.inj_series = g.wavelet_d;
+        df[i].info.inj_ncol = g.nsrc;
+        df[i].info.smp = reinterpret_cast<const PtEntry *>(base + L.tab + T.smp);
+        df[i].info.smp_out = g.traces_d;
+        df[i].info.smp_ncol = g.nrec;
+        da[i].info.inj = reinterpret_cast<const PtEntry *>(base + L.tab + T.ainj);
+        da[i].info.inj_series = g.resid_d;
+        da[i].info.inj_ncol = g.nrec;
+        da[i].info.gacc = b.gacc;
+        const int32_t *hip = reinterpret_cast<const int32_t *>(T.blob.data() + T.inj_ptr);
+        const int32_t *hsp = reinterpret_cast<const int32_t *>(T.blob.data() + T.smp_ptr);
+        const int32_t *hap = reinterpret_cast<const int32_t *>(T.blob.data() + T.ainj_ptr);
+        for (int t = 0; t < geo[i].ntiles; ++t) {
+            TileRec r;
+            std::memset(&r, 0, sizeof r);
+            r.shot = i;
+            r.tile = t;
+            r.x0 = (t % geo[i].tiles_x) * geo[i].tx;
+            r.z0 = (t / geo[i].tiles_x) * geo[i].tz;
+            TileRec a = r;
+            r.ib = g.nsrc ? hip[t] : 0;
+            r.ie = g.nsrc ? hip[t + 1] : 0;
+            TileRec c = r;            // recompute: no sampling
+            r.sb = (g.nrec && g.traces_d) ? hsp[t] : 0;
+            r.se = (g.nrec && g.traces_d) ? hsp[t + 1] : 0;
+            a.ib = g.nrec ? hap[t] : 0;
+            a.ie = g.nrec ? hap[t + 1] : 0;
+            rf.push_back(r);
+            rr.push_back(c);
+            ra.push_back(a);
+        }
+        base += L.total;
+    }
+    FDW_CK(cudaMemcpyAsync(xd, df.data(), nshots * sizeof(ShotDesc), cudaMemcpyHostToDevice, s));
+    FDW_CK(cudaMemcpyAsync(xa, da.data(), nshots * sizeof(ShotDesc), cudaMemcpyHostToDevice, s));
+    FDW_CK(cudaMemcpyAsync(xr, rf.data(), ntiles_all * sizeof(TileRec), cudaMemcpyHostToDevice, s));
+    FDW_CK(cudaMemcpyAsync(xr + rb, rr.data(), ntiles_all * sizeof(TileRec), cudaMemcpyHostToDevice, s));
+    FDW_CK(cudaMemcpyAsync(xr + 2 * rb, ra.data(), ntiles_all * sizeof(TileRec), cudaMemcpyHostToDevice, s));
+    BatchParams bp;
+    std::memset(&bp, 0, sizeof bp);
+    bp.ntiles = (int)ntiles_all;
+    bp.status = reinterpret_cast<int *>(ws);     // shot 0's status word
+    std::memcpy(bp.w, p0->W, sizeof bp.w);
+    const ShotDesc *dfd = reinterpret_cast<const ShotDesc *>(xd);
+    const ShotDesc *dad = reinterpret_cast<const ShotDesc *>(xa);
+    const TileRec *trf = reinterpret_cast<const TileRec *>(xr);
+    const TileRec *trr = reinterpret_cast<const TileRec *>(xr + rb);
+    const TileRec *tra = reinterpret_cast<const TileRec *>(xr + 2 * rb);
+    // forward sweep with checkpoints (u^n, u^{n-1}) at n = c k
+    bp.shots = dfd;
+    bp.tiles = trf;
+    for (int n = 0; n < nt; ++n) {
+        const int cur = n & 1;
+        if (n % k == 0)
+            for (int i = 0; i < nshots; ++i) {
+                const int c = n / k;
+                FDW_CK(cudaMemcpyAsync(sb[i].ckpt + (size_t)(2 * c) * sb[i].fb, sb[i].buf[cur], sb[i].fb,
+                                       cudaMemcpyDeviceToDevice, s));
+                FDW_CK(cudaMemcpyAsync(sb[i].ckpt + (size_t)(2 * c + 1) * sb[i].fb, sb[i].buf[cur ^ 1],
+                                       sb[i].fb, cudaMemcpyDeviceToDevice, s));
+            }
+        bp.step = n;
+        bp.parity = cur;
+        bp.seg = 0;
+        bp.check = check_step(n, nt);
+        FDW_CK(launch_batched2d(bv, bp, (int)ntiles_all, s, kModeForward));
+    }
+    // backward sweep over segments: restore, recompute storing D, adjoint steps
+    int t = 0;
+    for (int c = nck - 1; c >= 0; --c) {
+        const int k0 = c * k, k1 = std::min(k0 + k, nt);
+        for (int i = 0; i < nshots; ++i) {
+            FDW_CK(cudaMemcpyAsync(sb[i].buf[0], sb[i].ckpt + (size_t)(2 * c) * sb[i].fb, sb[i].fb,
+                                   cudaMemcpyDeviceToDevice, s));
+            FDW_CK(cudaMemcpyAsync(sb[i].buf[1], sb[i].ckpt + (size_t)(2 * c + 1) * sb[i].fb, sb[i].fb,
+                                   cudaMemcpyDeviceToDevice, s));
+        }
+        bp.shots = dfd;
+        bp.tiles = trr;
+        bp.check = 0;   // the recompute repeats the checked forward sweep bit for bit
+        for (int n = k0; n < k1; ++n) {
+            bp.step = n;
+            bp.parity = (n - k0) & 1;
+            bp.seg = n - k0;
+            FDW_CK(launch_batched2d(bv, bp, (int)ntiles_all, s, kModeStoreD));
+        }
+        bp.shots = dad;
+        bp.tiles = tra;
+        for (int j = k1; j > k0; --j, ++t) {
+            bp.step = j - 1;
+            bp.parity = t & 1;
+            bp.seg = j - 1 - k0;
+            bp.check = check_step(t, nt);
+            FDW_CK(launch_batched2d(bv, bp, (int)ntiles_all, s, kModeAdjoint));
+        }
+    }
+    for (int i = 0; i < nshots; ++i) {
+        const fd_plan *p = shots[i].plan;
+        const fd_problem &pr = p->prob;
+        const int64_t phys[3] = {pr.n[0], pr.n[1], pr.n[2]};
+        FDW_CK(launch_fold_grad(sb[i].gacc, p->pitch, zstride(p), phys, pr.nb, (float)(-1.0 / (pr.dt * pr.dt)),
+                                shots[i].grad_d, s));
+    }
     return FD_OK;
 }

@@ -256,6 +256,8 @@ __global__ void __launch_bounds__(kThreads) step2d_kernel(const __grid_constant_
 // ---------------------------------------------------------------------------
 struct BatchView {
     float *u_prev;
+    float *dseg;               // D of this step (store-D and adjoint modes)
+    float *gacc;
     int64_t nx, nz, pitch;
     int64_t phys_lo[3], phys_hi[3];
     float gcoef;
@@ -271,7 +273,8 @@ struct BatchView {
     int *status;
     const float (&w)[kWDim * kWDim];
     __device__ BatchView(const ShotInfo &d, const BatchParams &bp)
-        : u_prev(d.buf[(bp.step & 1) ^ 1]), nx(d.nx), nz(d.nz), pitch(d.pitch), gcoef(d.gcoef),
+        : u_prev(d.buf[bp.parity ^ 1]), dseg(d.dseg ? d.dseg + (int64_t)bp.seg * d.field : nullptr),
+          gacc(d.gacc), nx(d.nx), nz(d.nz), pitch(d.pitch), gcoef(d.gcoef),
           tiles_x(d.tiles_x), inj(d.inj), inj_series(d.inj_series), inj_ncol(d.inj_ncol),
           smp(d.smp), smp_out(d.smp_out), smp_ncol(d.smp_ncol), step(bp.step), check(bp.check),
           status(bp.status), w(bp.w)
@@ -308,8 +311,10 @@ struct StreamCfg {
     static constexpr int THREADS = kThreads + 32;
 };
 
-// Forward step of one staged tile.
-template <int SHAPE, int M, int R>
+// One step of one staged tile: forward (MODE kModeForward), forward storing
+// D = kappa lap (kModeStoreD) or adjoint with the gradient accumulation
+// (kModeAdjoint), with the arithmetic of step2d_tile in each mode.
+template <int SHAPE, int M, int R, int MODE>
 __device__ __forceinline__ void stream_tile(const BatchView &v, const Staged &st,
                                             const float *slot, int tx, int ty)
 {
@@ -331,15 +336,16 @@ __device__ __forceinline__ void stream_tile(const BatchView &v, const Staged &st
         const float uu[4] = {up.x, up.y, up.z, up.w};
         const float kk[4] = {kp.x, kp.y, kp.z, kp.w};
         const float d2z = layer_d2(zg, v.phys_lo[2], v.phys_hi[2]);
-        float o[4], g[4];
+        float o[4], dv[4], g[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             g[j] = v.gcoef * (d2x[j] + d2z);
-            step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
+            dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
         }
         if (st.rec.ib < st.rec.ie)
             for_row(v.inj, st.rec.ib, st.rec.ie, zg, tx, [&](int j, const PtEntry &en) {
-                const float a = en.scale * v.inj_series[(int64_t)v.step * v.inj_ncol + en.col];
+                float a = en.scale * v.inj_series[(int64_t)v.step * v.inj_ncol + en.col];
+                if (MODE == kModeAdjoint) a *= kk[j];
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
                     if (jj == j) o[jj] += a;
@@ -353,16 +359,28 @@ __device__ __forceinline__ void stream_tile(const BatchView &v, const Staged &st
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
                     if (jj == j) s = o[jj];
-                v.smp_out[(int64_t)v.step * v.smp_ncol + en.col] = s * en.scale;
+                s *= en.scale;
+                if (MODE == kModeAdjoint) s /= kk[j];
+                v.smp_out[(int64_t)v.step * v.smp_ncol + en.col] = s;
             });
         if (!colok || zg >= v.nz) continue;
+        const int64_t off = (int64_t)zg * v.pitch + xg;
         const float4 un = make_float4(o[0], o[1], o[2], o[3]);
         if (v.check) check_growth(v.status, un);
-        *reinterpret_cast<float4 *>(v.u_prev + (int64_t)zg * v.pitch + xg) = un;
+        *reinterpret_cast<float4 *>(v.u_prev + off) = un;
+        if (MODE == kModeStoreD)
+            *reinterpret_cast<float4 *>(v.dseg + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+        if (MODE == kModeAdjoint) {
+            const float4 d = ldg4(v.dseg + off);
+            float4 ga = *reinterpret_cast<float4 *>(v.gacc + off);
+            ga.x = fmaf(un.x, d.x, ga.x); ga.y = fmaf(un.y, d.y, ga.y);
+            ga.z = fmaf(un.z, d.z, ga.z); ga.w = fmaf(un.w, d.w, ga.w);
+            *reinterpret_cast<float4 *>(v.gacc + off) = ga;
+        }
     }
 }
 
-template <int SHAPE, int M, int R>
+template <int SHAPE, int M, int R, int MODE>
 __global__ void __launch_bounds__(StreamCfg<M, R>::THREADS)
 step2d_batched(const __grid_constant__ BatchParams bp)
 {
@@ -384,7 +402,7 @@ step2d_batched(const __grid_constant__ BatchParams bp)
     }
     __syncthreads();
     const int G = gridDim.x;
-    const int cur = bp.step & 1;
+    const int cur = bp.parity;
 
     if (warp == C::NCW) {   // producer: lane 0 waits and issues, the warp copies
         volatile int *abort_v = &abort_flag;
@@ -439,7 +457,7 @@ step2d_batched(const __grid_constant__ BatchParams bp)
         ok = mbar_wait_bounded(&full[b], (i / NB) & 1);
         if (!ok) break;
         const BatchView v(staged[b].info, bp);
-        stream_tile<SHAPE, M, R>(v, staged[b], sm + b * C::SLOT, tx, ty);
+        stream_tile<SHAPE, M, R, MODE>(v, staged[b], sm + b * C::SLOT, tx, ty);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
     }
@@ -935,10 +953,20 @@ KernelFn lookup_fast(int shape, int M, int R, int mode)
 
 using BatchFn = void (*)(const BatchParams);
 
-BatchFn lookup_batched(int shape, int M, int R)
+template <int S, int MM, int RR>
+BatchFn pick_batched(int mode)
+{
+    switch (mode) {
+    case kModeForward: return step2d_batched<S, MM, RR, kModeForward>;
+    case kModeStoreD: return step2d_batched<S, MM, RR, kModeStoreD>;
+    default: return step2d_batched<S, MM, RR, kModeAdjoint>;
+    }
+}
+
+BatchFn lookup_batched(int shape, int M, int R, int mode = kModeForward)
 {
 #define FDW_B(S, MM, RR) \
-    if (shape == S && M == MM && R == RR) return step2d_batched<S, MM, RR>;
+    if (shape == S && M == MM && R == RR) return pick_batched<S, MM, RR>(mode);
     FDW_B(FD_CROSS, 2, 2) FDW_B(FD_CROSS, 4, 2) FDW_B(FD_CROSS, 8, 2)
 #undef FDW_B
     return nullptr;
@@ -1013,9 +1041,10 @@ int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v)
     return FD_OK;
 }
 
-cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s)
+cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s,
+                             int mode)
 {
-    BatchFn fn = lookup_batched(v.shape, v.M, v.tz / kTZ);
+    BatchFn fn = lookup_batched(v.shape, v.M, v.tz / kTZ, mode);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
     if (e != cudaSuccess) return e;

@@ -10,104 +10,12 @@
 // kernels: step3d_cross (z arm in a register queue) and step3d_planar
 // (rhombus and square: each plane scattered into a register accumulator of the
 // outputs it touches).
-#include "device_common.cuh"
+#include "step3d_common.cuh"
 
 namespace fdw {
 
 namespace {
 
-constexpr int kTX3 = 64;
-
-// CTAs per SM the warp-specialised pipelines are built for: 2 with 64 x 16
-// tiles; with 64 x 8 tiles 4 for the cross up to M = 4 (96 registers per
-// thread suffice) and 3 otherwise (the planar kernels run faster with the
-// registers of 3).
-__host__ __device__ constexpr int ctas_per_sm(bool cross, int M, int ty)
-{
-    return ty >= 16 ? 2 : (cross && M <= 4 ? 4 : 3);
-}
-
-// Ring depth: as many plane slots (4 to 8) as fit the shared memory of one
-// CTA at that residency; deeper rings keep more planes of copies in flight.
-__host__ __device__ constexpr int ring_depth(int slot_floats, int ctas)
-{
-    const int budget = (ctas <= 2 ? 80 : ctas == 3 ? 72 : 54) * 1024;
-    const int n = budget / (slot_floats * 4);
-    return n < 4 ? 4 : n > 8 ? 8 : n;
-}
-
-// Tile table walk for one plane: apply f(j, entry) to this thread's entries
-// with entry.z == z.  Entries are sorted by (z, y, x) within a tile, so the
-// plane's segment and, inside it, this thread's row and 4 columns are found
-// by binary search; `k` advances to the first entry of a later plane.
-__device__ __forceinline__ long long entry_key(int z, int yx)
-{
-    return ((long long)z << 32) | (unsigned)yx;
-}
-
-__device__ __forceinline__ int first_at_least(const PtEntry *tab, int lo, int hi, long long key)
-{
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (entry_key(tab[mid].z, tab[mid].yx) < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-template <class F>
-__device__ __forceinline__ void plane_entries(const PtEntry *tab, int &k, int kend, int z,
-                                              int tx, int ty, F f)
-{
-    const int zb = first_at_least(tab, k, kend, entry_key(z, 0));
-    const int ze = first_at_least(tab, zb, kend, entry_key(z + 1, 0));
-    const int lo = (ty << 16) | (4 * tx), hi = lo + 4;
-    for (int i = first_at_least(tab, zb, ze, entry_key(z, lo)); i < ze; ++i) {
-        const PtEntry en = tab[i];
-        if (en.yx >= hi) break;
-        f(en.yx & 3, en);
-    }
-    k = ze;
-}
-
-// Out-of-line handlers for the (rare) planes that carry table entries, so the
-// unrolled plane loops stay small.  Everything goes in and out by value (a
-// reference would force the caller's registers into local memory every
-// plane); they return the next pending entry and its z.
-struct InjOut {
-    float4 o;
-    int k, z;
-};
-
-template <int MODE>
-__device__ __noinline__ InjOut inject_plane(const StepParams &p, int k, int kend, int z, int tx,
-                                            int ty, float4 o, float4 kk)
-{
-    plane_entries(p.inj, k, kend, z, tx, ty, [&](int j, const PtEntry &en) {
-        float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
-        if (MODE == kModeAdjoint) a *= get4(kk, j);
-        add4(o, j, a);
-    });
-    InjOut r;
-    r.o = o;
-    r.k = k;
-    r.z = k < kend ? p.inj[k].z : 0x7fffffff;
-    return r;
-}
-
-template <int MODE>
-__device__ __noinline__ int2 sample_plane(const StepParams &p, int k, int kend, int z, int tx,
-                                          int ty, float4 o, float4 kk)
-{
-    plane_entries(p.smp, k, kend, z, tx, ty, [&](int j, const PtEntry &en) {
-        float v = get4(o, j) * en.scale;
-        if (MODE == kModeAdjoint) v /= get4(kk, j);
-        p.smp_out[(int64_t)p.step * p.smp_ncol + en.col] = v;
-    });
-    return make_int2(k, k < kend ? p.smp[k].z : 0x7fffffff);
-}
-
-using KernelFn = void (*)(const StepParams);
 
 
 
@@ -241,9 +149,10 @@ step3d_cross(const __grid_constant__ StepParams p)
 
     // Queue of centre values as packed pairs (x, y) and (z, w).  Unrolled
     // (M <= 4): the plane fed at stream index s sits in slot s mod QL and the
-    // loop is unrolled by QL.  Blocked (M >= 6, to keep the code small): the
-    // loop is unrolled by UF = 3 over a queue of QL + 2 slots that moves down
-    // UF slots at the start of each block; sub-step uu feeds slot QL-1+uu.
+    // loop is unrolled by QL.  Blocked (M >= 6, smaller code and, measured on
+    // the 460^3 grid, the same speed as the unrolled form): the loop is
+    // unrolled by UF = 3 over a queue of QL + 2 slots that moves down UF slots
+    // at the start of each block; sub-step uu feeds slot QL-1+uu.
     constexpr bool kUnroll = M <= 4;
     constexpr int UF = kUnroll ? QL : 3;
     constexpr int QN = kUnroll ? QL : QL + UF - 1;
@@ -713,11 +622,10 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
     v->M = M;
     v->N = N;
     v->generic = 0;
-    int ty = ty_pref > 0 ? ty_pref : (M <= 4 ? 16 : 8);
+    const int ty = ty_pref > 0 ? ty_pref : (M <= 4 ? 16 : 8);
     if (!lookup3(shape, M, ty, 0)) return FD_ERR_UNSUPPORTED;
     v->tx = kTX3;
     v->tz = ty;
-    v->threads = 16 * ty;
     const int HX = round4(M);
     v->box[0] = kTX3 + 2 * HX;
     v->box[1] = ty + 2 * M;
@@ -725,9 +633,9 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
     v->tbox[0] = kTX3;
     v->tbox[1] = ty;
     {   // warp-specialised pipelines (cross and planar): one extra producer warp
-        const int HXc = round4(M);
-        const int A = ((kTX3 + 2 * HXc) * (ty + 2 * M) + 31) & ~31;
-        v->smem = (size_t)ring_depth(A + 3 * kTX3 * ty, ctas_per_sm(shape == FD_CROSS, M, ty)) * (A + 3 * kTX3 * ty) * sizeof(float);
+        const int A = ((kTX3 + 2 * HX) * (ty + 2 * M) + 31) & ~31;
+        v->smem = (size_t)ring_depth(A + 3 * kTX3 * ty, ctas_per_sm(shape == FD_CROSS, M, ty)) *
+                  (A + 3 * kTX3 * ty) * sizeof(float);
         v->threads = 16 * ty + 32;
     }
     (void)nx; (void)ny; (void)nz;
@@ -740,6 +648,19 @@ int variants_3d(int shape, int M, int *ty_out, int cap)
     for (int ty : {16, 8})
         if (n < cap && lookup3(shape, M, ty, 0)) ty_out[n++] = ty;
     return n;
+}
+
+// Resident CTAs per SM of a 3D variant's kernel (registers, shared memory and
+// threads all counted), 0 on error.
+int occupancy_3d(const Variant &v)
+{
+    KernelFn fn = lookup3(v.shape, v.M, v.tz, kModeForward);
+    if (!fn) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem) != cudaSuccess)
+        return 0;
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, v.threads, v.smem) != cudaSuccess) return 0;
+    return per;
 }
 
 cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s)

@@ -148,3 +148,77 @@ def test_shot_driver_on_the_gpu_matches_the_oracle_sum():
     J, g = misfit_and_gradient(m, 3, run)
     assert abs(J - J_o) < 1e-4 * J_o
     assert rel_l2(g.cpu().numpy(), g_o) < 1e-4
+
+
+@pytest.mark.parametrize("shape,M,scheme", [("rhombus", 4, "displs"), ("cross", 4, "spatte")])
+def test_gradient_is_bitwise_equal_across_3d_variants(shape, M, scheme):
+    """The forward, recompute and adjoint sweeps of every 3D kernel variant
+    give the same gradient bit for bit."""
+    import torch
+    import paper_2606_04882_gb300 as F
+    c = _case(3, 40, shape=shape, M=M, scheme=scheme)
+    resid = np.random.default_rng(2).standard_normal((c.nt, len(c.rec))).astype(np.float32)
+    plan = c.plan()
+    dev = torch.device("cuda")
+    m = torch.from_numpy(c.vel).to(dev)
+    wav = torch.from_numpy(c.wavelet32()).to(dev)
+    r = torch.from_numpy(resid).to(dev)
+    ref = None
+    for v in plan.variants():
+        plan.set_variant(v, 0)
+        g = torch.empty_like(m)
+        ws = F.workspace(plan.gradient_workspace_size(1, len(c.rec), 9))
+        F.fd_adjoint_gradient(plan, m, plan.linear_index(c.src), wav, plan.linear_index(c.rec), r, 9,
+                              g, ws)
+        assert F.fd_status_read(plan, ws) == 0
+        g = g.cpu().numpy()
+        if ref is None:
+            ref = g
+        assert np.array_equal(g, ref), v
+
+
+@pytest.mark.parametrize("shape,M,scheme", [("cross", 4, "spatte"), ("cross", 2, "spatte"),
+                                            ("rhombus", 4, "displs")])
+def test_batched_gradient_equals_per_shot_gradients(shape, M, scheme):
+    """fd_adjoint_gradient_batched over five shots on two grids of different
+    size (one launch per step over every shot's tiles for the cross; shot by
+    shot for the rhombus) gives each shot's gradient and traces bit for bit as
+    fd_adjoint_gradient does, and one shot matches the FP64 oracle."""
+    import torch
+    import paper_2606_04882_gb300 as F
+    dev = torch.device("cuda")
+    nt, nb, h, vmax, k = 90, 6, 10.0, 3000.0, 11
+    grids = [(61, 83), (45, 130)]
+    dt = min(Case(np.zeros(g, np.float32), h, nt, nb, vmax, "cross", M).dt for g in grids)
+    shots, ref = [], []
+    for i in range(5):
+        g = grids[i % 2]
+        vel = smooth_velocity(g, 30 + i, 1500.0, 2900.0, sigma=3.0)
+        rng = np.random.default_rng(40 + i)
+        rec = np.stack([np.full(20, 2), rng.integers(0, g[1], 20)], axis=1)
+        src = np.array([[3, (7 + 13 * i) % g[1]]])
+        c = Case(vel, h, nt, nb, vmax, shape, M, 0, scheme, src=src, rec=rec, f0=25.0, dt=dt)
+        plan = c.plan()
+        resid = torch.from_numpy(rng.standard_normal((nt, len(rec))).astype(np.float32)).to(dev)
+        d = dict(plan=plan, model=torch.from_numpy(c.vel).to(dev), src_idx=plan.linear_index(src),
+                 wavelet=torch.from_numpy(c.wavelet32()).to(dev), rec_idx=plan.linear_index(rec),
+                 resid=resid, grad=torch.full(g, float("nan"), device=dev),
+                 traces=torch.full((nt, len(rec)), float("nan"), device=dev))
+        shots.append(d)
+        g1 = torch.empty(g, device=dev)
+        tr1 = torch.zeros((nt, len(rec)), device=dev)
+        ws1 = F.workspace(plan.gradient_workspace_size(1, len(rec), k))
+        F.fd_adjoint_gradient(plan, d["model"], d["src_idx"], d["wavelet"], d["rec_idx"], resid, k, g1,
+                              ws1, traces=tr1)
+        assert F.fd_status_read(plan, ws1) == 0
+        ref.append((g1.cpu().numpy(), tr1.cpu().numpy(), c, resid.cpu().numpy()))
+    ws = F.workspace(F.batched_gradient_workspace_size(shots, k))
+    F.fd_adjoint_gradient_batched(shots, k, ws)
+    assert F.fd_status_read(shots[0]["plan"], ws) == 0
+    for d, (g1, tr1, _, _) in zip(shots, ref):
+        assert np.array_equal(d["grad"].cpu().numpy(), g1)
+        assert np.array_equal(d["traces"].cpu().numpy(), tr1)
+    g1, _, c, resid = ref[3]
+    og, _ = W.gradient(c.setup(), nt, c.src, P.ricker(c.f0, nt, c.dt)[:, None], c.rec,
+                       resid.astype(np.float64), threads=8)
+    assert rel_l2(g1, og) < 1e-4
