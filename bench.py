@@ -65,6 +65,7 @@ def dist_env():
 # scaled to the bench grid by its point count), valid only for the kernel
 # sources whose digest is recorded with them.
 TRAFFIC_SOURCES = ("paper_2606_04882_gb300/csrc/step3d.cu",
+                   "paper_2606_04882_gb300/csrc/step3d_common.cuh",
                    "paper_2606_04882_gb300/csrc/device_common.cuh",
                    "paper_2606_04882_gb300/csrc/internal.h")
 TRAFFIC_DIGEST = "67448eafb4897353668d2e5405ca7ccba9db0cceff205e4cc2e03a4842fde978"
@@ -435,6 +436,7 @@ def run_other(args):
             return shots
         shots, shots0 = make(nt), make(0)
         ws = F.workspace(max(F.batched_workspace_size(shots), F.batched_workspace_size(shots0)), dev)
+        F.fd_forward_batched_autotune(shots, ws)                 # untimed tile choice
         pts = 0
         for d in shots:
             inf = d["plan"].info()

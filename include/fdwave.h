@@ -333,6 +333,23 @@ int fd_forward_batched(int nshots, const fd_shot *shots, void *ws_d, size_t ws_b
                        void *stream);
 
 /*
+ * Tile shape of single-launch batches: the batched tile kernel has 64 x 16R
+ * tiles with R rows per thread (R = 2 by default, or 4).
+ * fd_forward_batched_autotune times each R on this batch (best of three
+ * 64-step runs minus best of three 16-step runs, launched step by step,
+ * copies of the plans) and keeps the fastest (a candidate must win by 2 %)
+ * for batches of the same stencil, shot count and total padded size on this
+ * device, for the rest of the process; fd_forward_batched_set_variant sets R
+ * by hand.  The batched gradient uses the same choice.  Results do not depend
+ * on R.  The workspace sizes above cover every R.  Synchronises `stream`.
+ * Errors: FD_ERR_ARG, FD_ERR_NOMEM, FD_ERR_CUDA, FD_ERR_UNSUPPORTED (R not
+ * built for the stencil).
+ */
+int fd_forward_batched_autotune(int nshots, const fd_shot *shots, void *ws_d, size_t ws_bytes,
+                                void *stream);
+int fd_forward_batched_set_variant(int nshots, const fd_shot *shots, int rows);
+
+/*
  * Batched gradients (the paper has no counterpart; its FWI outlook sums the
  * gradients of many shots): the checkpointed adjoint gradient of
  * fd_adjoint_gradient for several shots in one call, each shot with its own

@@ -102,6 +102,8 @@ _SIGS = {
     "fd_adjoint_gradient": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _P, _P, _SZ, _P]),
     "fd_forward_batched_workspace_size": (_I, [_I, _P, _P]),
     "fd_forward_batched": (_I, [_I, _P, _P, _SZ, _P]),
+    "fd_forward_batched_autotune": (_I, [_I, _P, _P, _SZ, _P]),
+    "fd_forward_batched_set_variant": (_I, [_I, _P, _I]),
     "fd_forward_noalloc": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _P, _P, _P]),
     "fd_adjoint_gradient_batched_workspace_size": (_I, [_I, _P, _I, _P]),
     "fd_adjoint_gradient_batched": (_I, [_I, _P, _I, _P, _SZ, _P]),
@@ -414,6 +416,32 @@ def fd_forward_batched(shots: Sequence[dict], ws, stream=None):
                          len(ri), 0, _addr(s["model"]), si.ctypes.data, _addr(s["wavelet"]),
                          ri.ctypes.data, _addr(s["traces"]))
     _check(lib().fd_forward_batched(len(shots), arr, _addr(ws), ws.numel(), _stream_ptr(stream)))
+
+
+def _fwd_shots(shots: Sequence[dict]):
+    arr = (fd_shot * len(shots))()
+    keep = []
+    for i, s in enumerate(shots):
+        si = np.ascontiguousarray(s["src_idx"], np.int64)
+        ri = np.ascontiguousarray(s["rec_idx"], np.int64)
+        keep += [si, ri]
+        arr[i] = fd_shot(s["plan"].ptr.value, s.get("model_kind", FD_MODEL_VELOCITY), len(si),
+                         len(ri), 0, _addr(s["model"]), si.ctypes.data, _addr(s["wavelet"]),
+                         ri.ctypes.data, _addr(s["traces"]))
+    return arr, keep
+
+
+def fd_forward_batched_autotune(shots: Sequence[dict], ws, stream=None):
+    """Time the batched kernel's tile shapes on this batch and keep the fastest."""
+    arr, keep = _fwd_shots(shots)
+    _check(lib().fd_forward_batched_autotune(len(shots), arr, _addr(ws), ws.numel(),
+                                             _stream_ptr(stream)))
+
+
+def fd_forward_batched_set_variant(shots: Sequence[dict], rows: int):
+    """Choose the batched kernel's rows per thread (2 or 4) for this batch."""
+    arr, keep = _fwd_shots(shots)
+    _check(lib().fd_forward_batched_set_variant(len(shots), arr, rows))
 
 
 def batched_workspace_size(shots: Sequence[dict]) -> int:

@@ -185,7 +185,8 @@ constexpr int kMaxVariants = 8;
 cudaError_t launch_step2d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
 cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
 int occupancy_3d(const Variant &v);
-int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v);
+int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v, int r_pref = 0);
+int batch2d_variants(int shape, int M, int *r_out, int cap);
 int persist2d_grid(const Variant &v, int ntiles);
 cudaError_t launch_persist2d(const Variant &v, const PersistParams &pp, int grid, cudaStream_t s);
 cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles, cudaStream_t s,

@@ -1126,7 +1126,37 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
 namespace {
 
 // Common batch variant for 2D shots (nullptr if the batch needs per-shot launches).
-bool batch_geometry(int nshots, const fd_shot *shots, Variant &bv, std::vector<TileGeo> &geo)
+// Tile rows per thread chosen for a batch by fd_forward_batched_autotune,
+// keyed by device, stencil, shot count and total padded points.
+std::mutex g_batch_mu;
+std::map<std::string, int> g_batch_tune;
+
+std::string batch_key(int nshots, const fd_shot *shots)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    int64_t pts = 0;
+    for (int i = 0; i < nshots; ++i) pts += shots[i].plan->pad[0] * shots[i].plan->pad[2];
+    const fd_plan *p0 = shots[0].plan;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|batch|%d|%d|%d|%lld", prop.name, p0->shape_eff, p0->st.M, nshots,
+             (long long)pts);
+    return buf;
+}
+
+int batch_choice(int nshots, const fd_shot *shots)
+{
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto it = g_batch_tune.find(batch_key(nshots, shots));
+    return it == g_batch_tune.end() ? 0 : it->second;
+}
+
+// Common single-launch variant of a 2D batch with R rows per thread (0: the
+// tuned or default choice); false if the batch needs per-shot launches.
+bool batch_geometry(int nshots, const fd_shot *shots, Variant &bv, std::vector<TileGeo> &geo,
+                    int R = 0)
 {
     const fd_plan *p0 = shots[0].plan;
     if (p0->prob.dim != 2 || p0->var.generic) return false;
@@ -1136,7 +1166,8 @@ bool batch_geometry(int nshots, const fd_shot *shots, Variant &bv, std::vector<T
         if (q->shape_eff != p0->shape_eff || q->st.M != p0->st.M || q->var.generic) return false;
         tiles4 += ((q->pad[2] + 63) / 64) * ((q->pad[0] + 63) / 64);
     }
-    if (batch2d_variant(p0->shape_eff, p0->st.M, tiles4, &bv)) return false;
+    if (R == 0) R = batch_choice(nshots, shots);
+    if (batch2d_variant(p0->shape_eff, p0->st.M, tiles4, &bv, R)) return false;
     geo.resize(nshots);
     for (int i = 0; i < nshots; ++i) {
         const fd_plan *q = shots[i].plan;
@@ -1178,16 +1209,15 @@ bool batch_two_step(const fd_plan *p0, bool one, Batch2Geo *g)
 
 }  // namespace
 
-extern "C" int fd_forward_batched_workspace_size(int nshots, const fd_shot *shots, size_t *bytes)
+namespace {
+
+// Workspace of a batch laid out for tile rows R (0: the tuned or default R).
+size_t batch_bytes(int nshots, const fd_shot *shots, int R)
 {
-    clear_error();
-    if (nshots < 0 || (nshots > 0 && !shots) || !bytes) return set_error(FD_ERR_ARG, "bad argument");
-    for (int i = 0; i < nshots; ++i)
-        if (!shots[i].plan) return set_error(FD_ERR_ARG, "shot %d has no plan", i);
     size_t tot = 0;
     Variant bv;
     std::vector<TileGeo> geo;
-    const bool one = nshots > 0 && batch_geometry(nshots, shots, bv, geo);
+    const bool one = nshots > 0 && batch_geometry(nshots, shots, bv, geo, R);
     int64_t ntiles = 0;
     for (int i = 0; i < nshots; ++i) {
         const int nt_tab = one ? geo[i].ntiles : -1;
@@ -1197,14 +1227,33 @@ extern "C" int fd_forward_batched_workspace_size(int nshots, const fd_shot *shot
     Batch2Geo g2;
     const bool two = nshots > 0 && batch_two_step(shots[0].plan, one, &g2);
     if (one) tot += batch_extra_bytes(nshots, shots, ntiles, two);
+    return tot;
+}
+
+}  // namespace
+
+extern "C" int fd_forward_batched_workspace_size(int nshots, const fd_shot *shots, size_t *bytes)
+{
+    clear_error();
+    if (nshots < 0 || (nshots > 0 && !shots) || !bytes) return set_error(FD_ERR_ARG, "bad argument");
+    for (int i = 0; i < nshots; ++i)
+        if (!shots[i].plan) return set_error(FD_ERR_ARG, "shot %d has no plan", i);
+    // enough for every tile shape the batch can take (the tuned one included)
+    size_t tot = batch_bytes(nshots, shots, 2);
+    if (nshots > 0) {
+        int rs[4];
+        const int nr = batch2d_variants(shots[0].plan->shape_eff, shots[0].plan->st.M, rs, 4);
+        for (int i = 0; i < nr; ++i) tot = std::max(tot, batch_bytes(nshots, shots, rs[i]));
+    }
     *bytes = tot;
     return FD_OK;
 }
 
-extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, size_t ws_bytes,
-                                  void *stream)
+namespace {
+
+int forward_batched_impl(int nshots, const fd_shot *shots, void *ws, size_t ws_bytes, void *stream,
+                         int R, bool graphs)
 {
-    clear_error();
     size_t need = 0;
     int st = fd_forward_batched_workspace_size(nshots, shots, &need);
     if (st) return st;
@@ -1221,9 +1270,10 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
     }
     Variant bv;
     std::vector<TileGeo> geo;
-    const bool one = batch_geometry(nshots, shots, bv, geo);
+    bool one = batch_geometry(nshots, shots, bv, geo, R);
     Batch2Geo g2;
     const bool two = batch_two_step(p0, one, &g2);
+    if (two && bv.tz != g2.tz) one = batch_geometry(nshots, shots, bv, geo, g2.tz / 16);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = reinterpret_cast<char *>(ws);
     // extra region (after every shot's slice): descriptors | tile records |
@@ -1414,7 +1464,33 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
         key.push_back(((uint64_t)(uint32_t)sh.nsrc << 32) | (uint32_t)sh.nrec);
     }
     key.push_back(two ? 1ull : 0ull);
+    key.push_back(((uint64_t)bv.tz << 32) | (uint32_t)p0->prob.nt);
     key.insert(key.begin(), 2ull);
+    if (!graphs) {   // launches one by one (autotuning: candidates with other nt or tiles)
+        cudaError_t ce = cudaSuccess;
+        const int nt = p0->prob.nt;
+        for (int n = 0; n < nt && ce == cudaSuccess; ++n) {
+            if (one) {
+                bp.step = n;
+                bp.parity = n & 1;
+                bp.check = check_step(n, nt);
+                ce = launch_batched2d(bv, bp, ntiles, s);
+                continue;
+            }
+            for (int i = 0; i < nshots && ce == cudaSuccess; ++i) {
+                StepParams &sp = sps[i];
+                const int cur = n & 1;
+                bind_maps(sp, mp[i], 2, cur, cur ^ 1);
+                sp.u_cur = cur ? Bs[i] : As[i];
+                sp.u_prev = cur ? As[i] : Bs[i];
+                sp.step = n;
+                sp.check = check_step(n, nt);
+                ce = launch(shots[i].plan, kModeForward, sp, s);
+            }
+        }
+        if (ce != cudaSuccess) return set_error(FD_ERR_CUDA, "batched launch failed: %s", cudaGetErrorString(ce));
+        return FD_OK;
+    }
     cudaGraphExec_t ge = graph_cache_find(key);
     if (!ge) {
         cudaStream_t cs;
@@ -1478,6 +1554,92 @@ extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, si
     return FD_OK;
 }
 
+}  // namespace
+
+extern "C" int fd_forward_batched(int nshots, const fd_shot *shots, void *ws, size_t ws_bytes,
+                                  void *stream)
+{
+    clear_error();
+    return forward_batched_impl(nshots, shots, ws, ws_bytes, stream, 0, true);
+}
+
+extern "C" int fd_forward_batched_set_variant(int nshots, const fd_shot *shots, int rows)
+{
+    clear_error();
+    if (nshots < 1 || !shots) return set_error(FD_ERR_ARG, "bad argument");
+    for (int i = 0; i < nshots; ++i)
+        if (!shots[i].plan) return set_error(FD_ERR_ARG, "shot %d has no plan", i);
+    int rs[4];
+    const int nr = batch2d_variants(shots[0].plan->shape_eff, shots[0].plan->st.M, rs, 4);
+    if (std::find(rs, rs + nr, rows) == rs + nr)
+        return set_error(FD_ERR_UNSUPPORTED, "no batched kernel with %d rows per thread for this stencil", rows);
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    g_batch_tune[batch_key(nshots, shots)] = rows;
+    return FD_OK;
+}
+
+extern "C" int fd_forward_batched_autotune(int nshots, const fd_shot *shots, void *ws, size_t ws_bytes,
+                                           void *stream)
+{
+    clear_error();
+    size_t need = 0;
+    int st = fd_forward_batched_workspace_size(nshots, shots, &need);
+    if (st) return st;
+    if (!ws || ws_bytes < need) return set_error(FD_ERR_NOMEM, "workspace too small (%zu < %zu)", ws_bytes, need);
+    if (nshots == 0) return FD_OK;
+    Variant bv;
+    std::vector<TileGeo> geo;
+    if (!batch_geometry(nshots, shots, bv, geo, 2)) return FD_OK;   // per-shot launches: nothing to choose
+    int rs[4];
+    const int nr = batch2d_variants(shots[0].plan->shape_eff, shots[0].plan->st.M, rs, 4);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // candidates run on copies of the plans with 16 and 64 steps, launched one
+    // by one (no graph); time per step = (best of 3 at 64 - best of 3 at 16) / 48
+    std::vector<fd_plan> copies(nshots);
+    std::vector<fd_shot> cs(shots, shots + nshots);
+    for (int i = 0; i < nshots; ++i) {
+        copies[i] = *shots[i].plan;
+        cs[i].plan = &copies[i];
+    }
+    cudaEvent_t e0, e1;
+    FDW_CK(cudaEventCreate(&e0));
+    FDW_CK(cudaEventCreate(&e1));
+    auto timed = [&](int R, int nt, float &out) -> int {
+        for (auto &c : copies) c.prob.nt = nt;
+        out = 1e30f;
+        for (int r = 0; r < 3; ++r) {
+            FDW_CK(cudaEventRecord(e0, s));
+            const int rc = forward_batched_impl(nshots, cs.data(), ws, ws_bytes, stream, R, false);
+            if (rc) return rc;
+            FDW_CK(cudaEventRecord(e1, s));
+            FDW_CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            FDW_CK(cudaEventElapsedTime(&t, e0, e1));
+            out = std::min(out, t);
+        }
+        return FD_OK;
+    };
+    float best = 1e30f;
+    int bestR = rs[0];
+    for (int i = 0; i < nr && !st; ++i) {
+        float t64 = 0.f, t16 = 0.f;
+        if ((st = timed(rs[i], 64, t64)) || (st = timed(rs[i], 16, t16))) break;
+        const float ms = (t64 - t16) / 48.f;
+        if (const char *vb = getenv("FDWAVE_TUNE_VERBOSE"))
+            if (vb[0] == '1') fprintf(stderr, "fdwave batch tune: R %d: %.4f ms per step\n", rs[i], ms);
+        if (ms < 0.98f * best) {
+            best = ms;
+            bestR = rs[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    g_batch_tune[batch_key(nshots, shots)] = bestR;
+    return FD_OK;
+}
+
 // ---------------------------- batched gradient ----------------------------
 // The checkpointed adjoint gradient of many shots.  For 2D shots of a cross
 // stencil with M = 2, 4 or 8 every step of each sweep (forward with
@@ -1527,11 +1689,18 @@ extern "C" int fd_adjoint_gradient_batched_workspace_size(int nshots, const fd_g
         return set_error(FD_ERR_ARG, "bad argument");
     for (int i = 0; i < nshots; ++i)
         if (!shots[i].plan) return set_error(FD_ERR_ARG, "shot %d has no plan", i);
-    Variant bv;
-    std::vector<TileGeo> geo;
+    // enough for every tile shape the batch can take (the tuned one included)
     std::vector<fd_shot> fs = as_shots(nshots, shots);
-    const bool one = nshots > 0 && batch_geometry(nshots, fs.data(), bv, geo);
-    *bytes = grad_batch_bytes(nshots, shots, ckpt_every, one, geo, nullptr);
+    int rs[4] = {2};
+    const int nr = nshots > 0 ? batch2d_variants(shots[0].plan->shape_eff, shots[0].plan->st.M, rs, 4) : 0;
+    size_t tot = 0;
+    for (int i = 0; i < std::max(nr, 1); ++i) {
+        Variant bv;
+        std::vector<TileGeo> geo;
+        const bool one = nshots > 0 && batch_geometry(nshots, fs.data(), bv, geo, rs[i]);
+        tot = std::max(tot, grad_batch_bytes(nshots, shots, ckpt_every, one, geo, nullptr));
+    }
+    *bytes = tot;
     return FD_OK;
 }
 

@@ -968,6 +968,7 @@ BatchFn lookup_batched(int shape, int M, int R, int mode = kModeForward)
 #define FDW_B(S, MM, RR) \
     if (shape == S && M == MM && R == RR) return pick_batched<S, MM, RR>(mode);
     FDW_B(FD_CROSS, 2, 2) FDW_B(FD_CROSS, 4, 2) FDW_B(FD_CROSS, 8, 2)
+    FDW_B(FD_CROSS, 2, 4) FDW_B(FD_CROSS, 4, 4) FDW_B(FD_CROSS, 8, 4)
 #undef FDW_B
     return nullptr;
 }
@@ -1017,11 +1018,26 @@ cudaError_t launch_persist2d(const Variant &v, const PersistParams &pp, int grid
                                        args, v.smem, s);
 }
 
-int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v)
+template <int R>
+size_t batch_smem(int M)
 {
-    // 64 x 32 tiles (R = 2): small slots, so each CTA keeps several tiles of
-    // copies in flight while it computes one
-    const int R = 2;
+    return M == 2 ? StreamCfg<2, R>::SMEM : M == 4 ? StreamCfg<4, R>::SMEM : StreamCfg<8, R>::SMEM;
+}
+
+int batch2d_variants(int shape, int M, int *r_out, int cap)
+{
+    int n = 0;
+    for (int r : {2, 4})
+        if (n < cap && lookup_batched(shape, M, r)) r_out[n++] = r;
+    return n;
+}
+
+int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v, int r_pref)
+{
+    // default 64 x 32 tiles (R = 2): small slots, so each CTA keeps several
+    // tiles of copies in flight while it computes one; 64 x 64 (R = 4) has
+    // less halo per point and fewer, larger copies
+    const int R = r_pref > 0 ? r_pref : 2;
     (void)total_tiles4;
     if (!lookup_batched(shape, M, R)) return FD_ERR_UNSUPPORTED;
     v->dim = 2;
@@ -1037,7 +1053,7 @@ int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v)
     v->box[2] = 1;
     v->tbox[0] = kTX;
     v->tbox[1] = kTZ * R;
-    v->smem = M == 2 ? StreamCfg<2, 2>::SMEM : M == 4 ? StreamCfg<4, 2>::SMEM : StreamCfg<8, 2>::SMEM;
+    v->smem = R == 4 ? batch_smem<4>(M) : batch_smem<2>(M);
     return FD_OK;
 }
 

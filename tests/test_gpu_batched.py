@@ -43,7 +43,7 @@ def _shots(M=4, scheme="spatte", dim=2, nt=120):
     return cases
 
 
-def _batched(cases, repeat=1):
+def _batched(cases, repeat=1, rows=0, autotune=False):
     import torch
     import paper_2606_04882_gb300 as F
     dev = torch.device("cuda")
@@ -56,6 +56,10 @@ def _batched(cases, repeat=1):
                  traces=tr)
         shots.append(d)
     ws = F.workspace(F.batched_workspace_size(shots))
+    if rows:
+        F.fd_forward_batched_set_variant(shots, rows)
+    if autotune:
+        F.fd_forward_batched_autotune(shots, ws)
     outs = []
     for _ in range(repeat):
         for d in shots:
@@ -107,3 +111,17 @@ def test_batched_3d_per_shot_launches():
     for i, c in enumerate(cases):
         tr, _, _ = c.gpu_forward()
         assert rel_l2(outs[0][i], tr) < 1e-6, i
+
+
+@pytest.mark.parametrize("M", [2, 4, 8])
+def test_batched_tile_shapes_and_autotune_keep_the_bits(M):
+    """Every tile shape of the batched kernel (R = 2 and 4 rows per thread, set
+    by hand) and the autotuner's choice give the single-shot traces bit for
+    bit, on a first call and on a graph replay."""
+    cases = _shots(M, "spatte", nt=70)
+    ref = [c.gpu_forward()[0] for c in cases]
+    for kw in (dict(rows=4), dict(rows=2), dict(autotune=True)):
+        outs = _batched(cases, repeat=2, **kw)
+        for i in range(len(cases)):
+            assert np.array_equal(outs[0][i], ref[i]), (kw, i)
+            assert np.array_equal(outs[1][i], ref[i]), (kw, i)

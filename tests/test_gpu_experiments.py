@@ -71,3 +71,61 @@ def test_short_sweep_of_both_models():
                 vals = [r[k] for k in ("snap_l2", "trace_l2", "gamma_dft", "gamma_cwt")]
                 assert all(np.isfinite(v) and v >= 0 for v in vals)
                 assert 0 < r["snap_rel_l2"] < 10
+
+
+@pytest.mark.parametrize("label,shape,M,N,scheme", [("DispLS-CrossRb(4,4)", "cross_rhombus", 4, 4, "displs"),
+                                                   ("SpatTE-Cross(4)", "cross", 4, 0, "spatte")])
+def test_homogeneous_coarse_run_and_its_norms_match_the_oracle(label, shape, M, N, scheme):
+    """One coarse run of the homogeneous experiment (Table table1:homogeneo at
+    the paper's size: 401^2 nodes plus the sponge, 1500 steps) through the
+    sweep's own path, against the FP64 oracle on the same inputs: the snapshot
+    at 1.05 s and the trace at (x, z) = (1200, 3000) m to relative L2 1e-4.
+    Then the Section 5.3 error norms and the Appendix A DFT dispersion norm
+    that the sweep reports for this scheme (GPU metrics against a 2x-refined
+    GPU reference) agree with the oracle's metrics of the oracle's run against
+    the same reference."""
+    import torch
+    import paper_2606_04882_gb300 as F
+    from paper_2606_04882_gb300 import experiments as E
+    from oracle import metrics as OM
+    from oracle import physics as P
+    from oracle import wave as W
+    ex = E.homogeneous()
+    dev = torch.device("cuda")
+    C = ex.vmax * ex.dt / ex.h
+    vc = torch.from_numpy(ex.model(1)).to(dev)
+    snap, tr, st = E._run(ex, 1, F.stencil_desc(2, shape, M, N, scheme, courant=C), vc,
+                          ex.node(ex.trace, 1), dev)
+    assert st == 0
+    snap, tr = snap.cpu().numpy(), tr.cpu().numpy()
+    # the oracle: the same two segments (snapshot step, then the rest)
+    setup = W.Setup(ex.model(1), ex.h, ex.dt, ex.nb, ex.vmax, 2, shape, M, N, scheme)
+    wav = P.ricker(ex.f0, ex.nt, ex.dt)[:, None]
+    src = np.array([ex.node(ex.src, 1)])
+    rec = np.array([ex.node(ex.trace, 1)])
+    n1 = ex.n_snap
+    tr1, u, um = W.forward(setup, n1, src, wav[:n1], rec, threads=16)
+    tr2, _, _ = W.forward(setup, ex.nt - n1, src, wav[n1:], rec, u0=u, um1=um, threads=16)
+    otr = np.concatenate([tr1, tr2])[:, 0]
+    nb = ex.nb
+    osnap = u[nb:nb + ex.n, nb:nb + ex.n]
+    assert np.linalg.norm(snap - osnap) / np.linalg.norm(osnap) < 1e-4
+    assert np.linalg.norm(tr - otr) / np.linalg.norm(otr) < 1e-4
+    # norms against a 2x-refined reference, GPU metrics on the GPU run and
+    # oracle metrics on the oracle run
+    res = E.run(ex, refine=2, m_max=M, only=[label])
+    row = res["schemes"][0]
+    assert row["status"] == "ok"
+    vr = torch.from_numpy(ex.model(2)).to(dev)
+    snap_r, tr_r, st = E._run(ex, 2, F.stencil_desc(2, "cross", 8, 0, "spatte", courant=C), vr,
+                              ex.node(ex.trace, 2), dev)
+    assert st == 0
+    snap_ref = snap_r[::2, ::2].cpu().numpy().astype(np.float64)
+    tr_ref = tr_r[1::2].cpu().numpy().astype(np.float64)
+    s1, s2, sinf = OM.error_norms(osnap, snap_ref, *OM.snapshot_scales(ex.h))
+    t1, t2, tinf = OM.error_norms(otr, tr_ref, 1.0 / ex.dt ** 2, 1.0 / ex.dt)
+    for got, want in ((row["snap_l1"], s1), (row["snap_l2"], s2), (row["snap_linf"], sinf),
+                      (row["trace_l1"], t1), (row["trace_l2"], t2), (row["trace_linf"], tinf)):
+        assert abs(got - want) <= 1e-3 * abs(want), (got, want)
+    _, norms, _, _ = OM.dft_gamma(otr[:, None], tr_ref[:, None])
+    assert abs(row["gamma_dft"] - float(norms[0])) <= 1e-3 * float(norms[0]) + 1e-6

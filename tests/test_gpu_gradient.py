@@ -177,13 +177,15 @@ def test_gradient_is_bitwise_equal_across_3d_variants(shape, M, scheme):
         assert np.array_equal(g, ref), v
 
 
-@pytest.mark.parametrize("shape,M,scheme", [("cross", 4, "spatte"), ("cross", 2, "spatte"),
-                                            ("rhombus", 4, "displs")])
-def test_batched_gradient_equals_per_shot_gradients(shape, M, scheme):
+@pytest.mark.parametrize("shape,M,scheme,rows", [("cross", 4, "spatte", 2), ("cross", 4, "spatte", 4),
+                                                 ("cross", 2, "spatte", 2), ("cross", 8, "spatte", 4),
+                                                 ("rhombus", 4, "displs", 0)])
+def test_batched_gradient_equals_per_shot_gradients(shape, M, scheme, rows):
     """fd_adjoint_gradient_batched over five shots on two grids of different
-    size (one launch per step over every shot's tiles for the cross; shot by
-    shot for the rhombus) gives each shot's gradient and traces bit for bit as
-    fd_adjoint_gradient does, and one shot matches the FP64 oracle."""
+    size (one launch per step over every shot's tiles for the cross, with the
+    batched kernel's 64 x 32 or 64 x 64 tiles; shot by shot for the rhombus)
+    gives each shot's gradient and traces bit for bit as fd_adjoint_gradient
+    does, and one shot matches the FP64 oracle."""
     import torch
     import paper_2606_04882_gb300 as F
     dev = torch.device("cuda")
@@ -212,6 +214,8 @@ def test_batched_gradient_equals_per_shot_gradients(shape, M, scheme):
                               ws1, traces=tr1)
         assert F.fd_status_read(plan, ws1) == 0
         ref.append((g1.cpu().numpy(), tr1.cpu().numpy(), c, resid.cpu().numpy()))
+    if rows:
+        F.fd_forward_batched_set_variant(shots, rows)
     ws = F.workspace(F.batched_gradient_workspace_size(shots, k))
     F.fd_adjoint_gradient_batched(shots, k, ws)
     assert F.fd_status_read(shots[0]["plan"], ws) == 0
