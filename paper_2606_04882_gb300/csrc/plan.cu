@@ -452,10 +452,6 @@ extern "C" int fd_plan_create(const fd_problem *prob, const fd_stencil_desc *ste
         p->tiles_x = (int)((padx + p->var.tx - 1) / p->var.tx);
         p->tiles_y = (int)((padz + p->var.tz - 1) / p->var.tz);
     } else {
-        if (p->shape_eff == FD_CROSS_RHOMBUS || p->shape_eff == FD_CROSS_SQUARE || M > 8) {
-            delete p;
-            return set_error(FD_ERR_UNSUPPORTED, "3D kernels support cross, rhombus and square shapes with M <= 8");
-        }
         st = select_variant_3d(p->shape_eff, M, stencil->N, padx, pady, padz, &p->var);
         p->tiles_x = (int)((padx + p->var.tx - 1) / p->var.tx);
         p->tiles_y = (int)((pady + p->var.tz - 1) / p->var.tz);
@@ -696,7 +692,7 @@ extern "C" int fd_plan_set_variant(fd_plan *p, int variant, int z_chunk)
 {
     clear_error();
     if (!p || z_chunk < 0) return set_error(FD_ERR_ARG, "bad argument");
-    if (p->var.generic) return set_error(FD_ERR_UNSUPPORTED, "the generic 2D kernel has no variants");
+    if (p->var.generic) return set_error(FD_ERR_UNSUPPORTED, "the generic kernel has no variants");
     int prefs[kMaxVariants];
     const int np = p->prob.dim == 2 ? variants_2d(p->shape_eff, p->st.M, prefs, kMaxVariants)
                                     : variants_3d(p->shape_eff, p->st.M, prefs, kMaxVariants);

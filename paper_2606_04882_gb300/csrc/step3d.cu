@@ -149,10 +149,10 @@ step3d_cross(const __grid_constant__ StepParams p)
 
     // Queue of centre values as packed pairs (x, y) and (z, w).  Unrolled
     // (M <= 4): the plane fed at stream index s sits in slot s mod QL and the
-    // loop is unrolled by QL.  Blocked (M >= 6, smaller code and, measured on
-    // the 460^3 grid, the same speed as the unrolled form): the loop is
+    // loop is unrolled by QL.  Blocked (M >= 6, smaller code): the loop is
     // unrolled by UF = 3 over a queue of QL + 2 slots that moves down UF slots
-    // at the start of each block; sub-step uu feeds slot QL-1+uu.
+    // at the start of each block; sub-step uu feeds slot QL-1+uu.  (Either
+    // form for either M measured within 0.2 % of the other on the 460^3 grid.)
     constexpr bool kUnroll = M <= 4;
     constexpr int UF = kUnroll ? QL : 3;
     constexpr int QN = kUnroll ? QL : QL + UF - 1;
@@ -576,6 +576,128 @@ step3d_planar(const __grid_constant__ StepParams p)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Generic 3D kernel: every shape of Section 4.1 (as the union of the 2D shape
+// in the three coordinate planes) with any radius 1 <= M <= kMaxM, for the
+// stencils no specialised kernel covers.  It gathers the stencil from global
+// memory (L1/L2 cached, no staging), with the tile and z-chunk decomposition,
+// point tables and modes of the specialised kernels: a CTA walks the 64 x TY
+// column of its tile over its z-chunk, thread (tx, ty) owning 4 consecutive x
+// of row ty.  Centre-free like the others: every point enters as
+// u(x + o) - u(x), grouped by orbit, so a constant field gives exactly zero.
+// ---------------------------------------------------------------------------
+constexpr int kGenTY = 8;
+
+template <int MODE>
+__global__ void __launch_bounds__(16 * kGenTY) step3d_generic(const __grid_constant__ StepParams p,
+                                                              int shape, int M, int N)
+{
+    const int ntile = p.tiles_x * p.tiles_y;
+    const int tile = blockIdx.x % ntile, zc = blockIdx.x / ntile;
+    const int x0 = (tile % p.tiles_x) * kTX3, y0 = (tile / p.tiles_x) * kGenTY;
+    const int zb = zc * p.zchunk;
+    const int nz = (int)p.nz, ny = (int)p.ny, nx = (int)p.nx;
+    const int ze = min(nz, zb + p.zchunk);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int xg = x0 + 4 * tx, yg = y0 + ty;
+    const bool colok = xg < nx && yg < ny;
+    const int64_t colo = (int64_t)yg * p.pitch + xg;
+    float d2xy[4];
+    {
+        const float d2y = layer_d2(yg, p.phys_lo[1], p.phys_hi[1]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d2xy[j] = layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2y;
+    }
+    int ki = p.inj_ptr ? p.inj_ptr[tile] : 0, kie = p.inj_ptr ? p.inj_ptr[tile + 1] : 0;
+    int ks = p.smp_ptr ? p.smp_ptr[tile] : 0, kse = p.smp_ptr ? p.smp_ptr[tile + 1] : 0;
+    int zinj = ki < kie ? p.inj[ki].z : 0x7fffffff;
+    int zsmp = ks < kse ? p.smp[ks].z : 0x7fffffff;
+    // u at (z, y, x); zero outside the padded grid
+    auto at = [&](int z, int y, int x) -> float {
+        if ((unsigned)z >= (unsigned)nz || (unsigned)y >= (unsigned)ny || (unsigned)x >= (unsigned)nx) return 0.f;
+        return __ldg(p.u_cur + (int64_t)z * p.plane + (int64_t)y * p.pitch + x);
+    };
+    for (int z = zb; z < ze; ++z) {
+        float lap[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (colok) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int x = xg + j;
+                if (x >= nx) continue;
+                const float c = at(z, yg, x);
+                cc[j] = c;
+                float acc = 0.f;
+                for (int d = 1; d <= M; ++d) {   // axis orbit (d, 0, 0): six points
+                    const float s = ((at(z, yg, x + d) - c) + (at(z, yg, x - d) - c)) +
+                                    ((at(z, yg + d, x) - c) + (at(z, yg - d, x) - c)) +
+                                    ((at(z + d, yg, x) - c) + (at(z - d, yg, x) - c));
+                    acc = fmaf(p.w[d * kWDim], s, acc);
+                }
+                // off-axis points (a, b), a, b >= 1, of the 2D shape in the xy, xz and yz planes
+                for (int b = 1; b <= M; ++b) {
+                    const int E = shape_ext(shape, M, N, b);
+                    for (int a = 1; a <= E; ++a) {
+                        const float w = p.w[max(a, b) * kWDim + min(a, b)];
+                        float s = 0.f;
+#pragma unroll
+                        for (int sa = -1; sa <= 1; sa += 2)
+#pragma unroll
+                            for (int sb = -1; sb <= 1; sb += 2) {
+                                s += (at(z, yg + sb * b, x + sa * a) - c) +      // xy plane
+                                     (at(z + sb * b, yg, x + sa * a) - c) +      // xz plane
+                                     (at(z + sb * b, yg + sa * a, x) - c);       // yz plane
+                            }
+                        acc = fmaf(w, s, acc);
+                    }
+                }
+                lap[j] = acc;
+            }
+        }
+        const int64_t off = (int64_t)z * p.plane + colo;
+        float4 up = make_float4(0.f, 0.f, 0.f, 0.f), kk = up;
+        if (colok) {   // rows are padded to a multiple of 32 floats: the float4 stays in the row
+            up = ldg4(p.u_prev + off);
+            kk = ldg4(p.kappa + off);
+        }
+        const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
+        const float upa[4] = {up.x, up.y, up.z, up.w}, ka[4] = {kk.x, kk.y, kk.z, kk.w};
+        float o[4], dv[4], g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            g[j] = p.gcoef * (d2xy[j] + d2z);
+            dv[j] = step_update(cc[j], upa[j], ka[j], lap[j], g[j], o[j]);
+        }
+        float4 of = make_float4(o[0], o[1], o[2], o[3]);
+        if (z >= zinj) {
+            const InjOut r = inject_plane<MODE>(p, ki, kie, z, tx, ty, of, kk);
+            of = r.o;
+            ki = r.k;
+            zinj = r.z;
+        }
+        of.x = g[0] != 0.f ? __fdividef(of.x, 1.f + g[0]) : of.x;
+        of.y = g[1] != 0.f ? __fdividef(of.y, 1.f + g[1]) : of.y;
+        of.z = g[2] != 0.f ? __fdividef(of.z, 1.f + g[2]) : of.z;
+        of.w = g[3] != 0.f ? __fdividef(of.w, 1.f + g[3]) : of.w;
+        if (z >= zsmp) {
+            const int2 r = sample_plane<MODE>(p, ks, kse, z, tx, ty, of, kk);
+            ks = r.x;
+            zsmp = r.y;
+        }
+        if (!colok) continue;
+        if (p.check) check_growth(p.status, of);
+        *reinterpret_cast<float4 *>(p.u_prev + off) = of;
+        if (MODE != kModeAdjoint && p.dseg_out)
+            *reinterpret_cast<float4 *>(p.dseg_out + off) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+        if (MODE == kModeAdjoint) {
+            const float4 dd = ldg4(p.dseg_in + off);
+            float4 ga = *reinterpret_cast<float4 *>(p.gacc + off);
+            ga.x = fmaf(of.x, dd.x, ga.x); ga.y = fmaf(of.y, dd.y, ga.y);
+            ga.z = fmaf(of.z, dd.z, ga.z); ga.w = fmaf(of.w, dd.w, ga.w);
+            *reinterpret_cast<float4 *>(p.gacc + off) = ga;
+        }
+    }
+}
+
 template <int SHAPE, int M, int TY>
 KernelFn pick_planar(int mode)
 {
@@ -623,7 +745,19 @@ int select_variant_3d(int shape, int M, int N, int64_t nx, int64_t ny, int64_t n
     v->N = N;
     v->generic = 0;
     const int ty = ty_pref > 0 ? ty_pref : (M <= 4 ? 16 : 8);
-    if (!lookup3(shape, M, ty, 0)) return FD_ERR_UNSUPPORTED;
+    if (!lookup3(shape, M, ty, 0)) {
+        // no specialised kernel (or not this tile): the generic kernel
+        if (ty_pref > 0 && lookup3(shape, M, M <= 4 ? 16 : 8, 0)) return FD_ERR_UNSUPPORTED;
+        if (M < 1 || M > kMaxM) return FD_ERR_UNSUPPORTED;
+        v->generic = 1;
+        v->tx = kTX3;
+        v->tz = kGenTY;
+        v->box[0] = kTX3; v->box[1] = kGenTY; v->box[2] = 1;   // maps unused by the kernel
+        v->tbox[0] = kTX3; v->tbox[1] = kGenTY;
+        v->threads = 16 * kGenTY;
+        v->smem = 0;
+        return 0;
+    }
     v->tx = kTX3;
     v->tz = ty;
     const int HX = round4(M);
@@ -654,6 +788,13 @@ int variants_3d(int shape, int M, int *ty_out, int cap)
 // threads all counted), 0 on error.
 int occupancy_3d(const Variant &v)
 {
+    if (v.generic) {
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step3d_generic<kModeForward>, v.threads, 0) !=
+            cudaSuccess)
+            return 0;
+        return per;
+    }
     KernelFn fn = lookup3(v.shape, v.M, v.tz, kModeForward);
     if (!fn) return 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem) != cudaSuccess)
@@ -665,6 +806,14 @@ int occupancy_3d(const Variant &v)
 
 cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s)
 {
+    if (v.generic) {
+        void (*gfn)(const StepParams, int, int, int) =
+            mode == kModeAdjoint ? step3d_generic<kModeAdjoint> : step3d_generic<kModeForward>;
+        const int grid = p.tiles_x * p.tiles_y * p.nz_chunks;
+        if (grid <= 0) return cudaSuccess;
+        gfn<<<grid, v.threads, 0, s>>>(p, v.shape, v.M, v.N);
+        return cudaGetLastError();
+    }
     KernelFn fn = lookup3(v.shape, v.M, v.tz, mode);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e =
