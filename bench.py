@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-gradient", action="store_true",
                     help="3d: skip the FWI-gradient sub-record")
+    ap.add_argument("--variants", default="",
+                    help="3d: comma-separated y tiles (fd_plan_variants values) for the three "
+                         "stencils instead of autotuning, e.g. 16,8,8")
     return ap.parse_args()
 
 
@@ -152,12 +155,16 @@ def run_gpu(args):
     vel = torch.from_numpy(pr.vel).to(dev)
     src_idx, rec_idx = None, None
     runs = []
-    for shape, M, scheme in STENCILS:
+    fixed = [int(v) for v in args.variants.split(",")] if args.variants else None
+    for i, (shape, M, scheme) in enumerate(STENCILS):
         dt = taylor_dt(F, M, h, vmax)
         desc = F.stencil_desc(3, shape, M, 0, scheme, courant=vmax * dt / h)
         plan = F.Plan(pr.shape, h, dt, nt, nb, vmax, desc)
         plan0 = F.Plan(pr.shape, h, dt, 0, nb, vmax, desc)      # set-up only (nt = 0)
-        tile = list(plan.autotune(vel).tile)                     # untimed tile-shape choice
+        if fixed:                                                # a given tile, cost-model z-chunk
+            tile = list(plan.set_variant(fixed[i], 0).tile)
+        else:
+            tile = list(plan.autotune(vel).tile)                 # untimed tile-shape choice
         if src_idx is None:
             src_idx = plan.linear_index(pr.src)
             rec_idx = plan.linear_index(pr.rec)

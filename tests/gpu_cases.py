@@ -15,6 +15,19 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def per_receiver_errors(tr, otr, floor=1e-3):
+    """Relative L2 error of each receiver's trace [nt, nrec], with the
+    denominator floored at `floor` times the largest trace norm (receivers the
+    wave barely reaches carry the FP32 noise of the field around them, not of
+    their own small signal).  One wrong receiver among many shows here even
+    when the global norm hides it."""
+    tr = np.asarray(tr, np.float64)
+    otr = np.asarray(otr, np.float64)
+    e = np.linalg.norm(tr - otr, axis=0)
+    o = np.linalg.norm(otr, axis=0)
+    return e / np.maximum(o, floor * (o.max() if o.size else 1.0))
+
+
 def taylor_dt(dim, M, h, vmax, frac=0.5):
     """dt = frac * C_max(Taylor cross of radius M) * h / vmax (oracle bound)."""
     pw = S.expand(dim, "cross", M, 0, S.weights(dim, "cross", M))

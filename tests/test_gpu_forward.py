@@ -7,7 +7,7 @@ and length."""
 import numpy as np
 import pytest
 
-from gpu_cases import Case, rel_l2
+from gpu_cases import Case, per_receiver_errors, rel_l2
 from workloads import homogeneous_2d, smooth_velocity
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +47,7 @@ def test_forward_2d_matches_oracle(shape, M, N, scheme):
     assert rc == 0
     otr, ost = c.oracle_forward(threads=8)
     assert rel_l2(tr, otr) < TOL
+    assert per_receiver_errors(tr, otr).max() < 10 * TOL
     assert rel_l2(st[0], ost[0]) < TOL and rel_l2(st[1], ost[1]) < TOL
 
 
@@ -66,6 +67,7 @@ def test_forward_3d_matches_oracle(shape, M, scheme):
     assert rc == 0
     otr, ost = c.oracle_forward(threads=8)
     assert rel_l2(tr, otr) < TOL
+    assert per_receiver_errors(tr, otr).max() < 10 * TOL
     assert rel_l2(st[0], ost[0]) < TOL
 
 

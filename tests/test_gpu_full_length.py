@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import workloads as WL
-from gpu_cases import Case, rel_l2
+from gpu_cases import Case, per_receiver_errors, rel_l2
 
 pytestmark = pytest.mark.gpu
 opt_in = pytest.mark.skipif(os.environ.get("FDWAVE_FULL_LENGTH") != "1",
@@ -36,17 +36,6 @@ def _case(pr, st):
     dt = 0.5 * F.fd_cfl_limit(F.stencil_desc(pr.dim, "cross", st.M)) * pr.h / pr.vmax
     return Case(pr.vel, pr.h, pr.nt, pr.nb, pr.vmax, st.shape, st.M, st.N, st.scheme,
                 src=pr.src, rec=pr.rec, f0=pr.f0, dt=dt)
-
-
-def per_receiver_errors(tr, otr):
-    """Relative L2 error of each receiver's trace, with the denominator floored
-    at 1e-3 of the largest trace norm (receivers the wave barely reaches carry
-    FP32 noise of the field around them, not of their own small signal)."""
-    tr = np.asarray(tr, np.float64)
-    otr = np.asarray(otr, np.float64)
-    e = np.linalg.norm(tr - otr, axis=0)
-    o = np.linalg.norm(otr, axis=0)
-    return e / np.maximum(o, 1e-3 * o.max())
 
 
 @pytest.mark.parametrize("k", [0, pytest.param(1, marks=opt_in), pytest.param(2, marks=opt_in)])
