@@ -185,6 +185,10 @@ constexpr int kMaxVariants = 8;
 cudaError_t launch_step2d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
 cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaStream_t s);
 int occupancy_3d(const Variant &v);
+// Every step of a single-launch batch in one cooperative launch (grid barrier
+// between steps; the status block of bp.status holds its words).
+cudaError_t launch_batched2d_persistent(const Variant &v, const BatchParams &bp, int ntiles, int nt,
+                                       cudaStream_t s);
 int batch2d_variant(int shape, int M, int64_t total_tiles4, Variant *v, int r_pref = 0);
 int batch2d_variants(int shape, int M, int *r_out, int cap);
 int persist2d_grid(const Variant &v, int ntiles);

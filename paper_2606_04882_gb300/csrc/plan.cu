@@ -1462,6 +1462,13 @@ int forward_batched_impl(int nshots, const fd_shot *shots, void *ws, size_t ws_b
     key.push_back(two ? 1ull : 0ull);
     key.push_back(((uint64_t)bv.tz << 32) | (uint32_t)p0->prob.nt);
     key.insert(key.begin(), 2ull);
+    {   // every step in one persistent launch (opt-in: FDWAVE_BATCH_PERSISTENT=1)
+        const char *e = std::getenv("FDWAVE_BATCH_PERSISTENT");
+        if (e && e[0] == '1' && one && !two) {
+            FDW_CK(launch_batched2d_persistent(bv, bp, ntiles, p0->prob.nt, s));
+            return FD_OK;
+        }
+    }
     if (!graphs) {   // launches one by one (autotuning: candidates with other nt or tiles)
         cudaError_t ce = cudaSuccess;
         const int nt = p0->prob.nt;

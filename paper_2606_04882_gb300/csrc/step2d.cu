@@ -273,10 +273,14 @@ struct BatchView {
     int *status;
     const float (&w)[kWDim * kWDim];
     __device__ BatchView(const ShotInfo &d, const BatchParams &bp)
-        : u_prev(d.buf[bp.parity ^ 1]), dseg(d.dseg ? d.dseg + (int64_t)bp.seg * d.field : nullptr),
+        : BatchView(d, bp, bp.step, bp.parity, bp.check) {}
+    // the same with the step, field parity and growth check given explicitly
+    // (the persistent batched kernel advances them itself)
+    __device__ BatchView(const ShotInfo &d, const BatchParams &bp, int step_, int parity, int check_)
+        : u_prev(d.buf[parity ^ 1]), dseg(d.dseg ? d.dseg + (int64_t)bp.seg * d.field : nullptr),
           gacc(d.gacc), nx(d.nx), nz(d.nz), pitch(d.pitch), gcoef(d.gcoef),
           tiles_x(d.tiles_x), inj(d.inj), inj_series(d.inj_series), inj_ncol(d.inj_ncol),
-          smp(d.smp), smp_out(d.smp_out), smp_ncol(d.smp_ncol), step(bp.step), check(bp.check),
+          smp(d.smp), smp_out(d.smp_out), smp_ncol(d.smp_ncol), step(step_), check(check_),
           status(bp.status), w(bp.w)
     {
         for (int i = 0; i < 3; ++i) {
@@ -464,6 +468,150 @@ step2d_batched(const __grid_constant__ BatchParams bp)
     if (!ok) {
         atomicOr(bp.status, kStatusTimeout);
         *reinterpret_cast<volatile int *>(&abort_flag) = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched shots, every time step in one persistent launch.  A cooperative
+// launch keeps all CTAs resident; each walks its share of the tile table for
+// step n through the same producer/consumer ring as step2d_batched (the ring
+// position carries over from step to step), then the CTAs meet at a grid
+// barrier before step n + 1 reads what step n wrote.  The barrier's words are
+// the status block's words 1 (abort), 2 (count) and 3 (generation).  Every
+// wait is bounded: a time-out sets the status bit and the abort word, the
+// producer lets its copies in flight land, and every CTA leaves at its next
+// barrier.  The TMA-issuing lane orders the previous step's generic-proxy
+// writes before its async-proxy reads with a proxy fence after the barrier.
+// Same per-point arithmetic as the per-step kernel, so the same bits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool batch_grid_sync(const BatchParams &bp, bool local_abort)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = local_abort ? 0 : 1;
+        volatile int *abort_g = bp.status + 1;
+        unsigned int *count = reinterpret_cast<unsigned int *>(bp.status + 2);
+        volatile unsigned int *gen = reinterpret_cast<volatile unsigned int *>(bp.status + 3);
+        if (!ok) {
+            *abort_g = 1;
+        } else {
+            const unsigned int g = *gen;
+            __threadfence();
+            const unsigned int a = atomicAdd(count, 1u) + 1u;
+            if (a == gridDim.x) {
+                atomicExch(count, 0u);
+                __threadfence();
+                atomicAdd(reinterpret_cast<unsigned int *>(bp.status + 3), 1u);
+            } else {
+                const long long t0 = clock64();
+                while (*gen == g) {
+                    if (*abort_g) {
+                        ok = 0;
+                        break;
+                    }
+                    if (clock64() - t0 > kWaitCycles) {
+                        atomicOr(bp.status, kStatusTimeout);
+                        *abort_g = 1;
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <int SHAPE, int M, int R>
+__global__ void __launch_bounds__(StreamCfg<M, R>::THREADS)
+step2d_batched_persistent(const __grid_constant__ BatchParams bp, int nt)
+{
+    using C = StreamCfg<M, R>;
+    constexpr int NB = C::NB;
+    constexpr uint32_t BYTES = (C::SW * C::SH + 2 * C::TEL) * 4;
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t full[NB], empty[NB];
+    __shared__ Staged staged[NB];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < NB; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], C::NCW);
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int G = gridDim.x;
+    volatile int *abort_v = &abort_flag;
+    const int tx = tid & 15, ty = tid >> 4;
+    int i = 0;   // ring position; producer and consumers count the same tiles
+    for (int n = 0; n < nt; ++n) {
+        const int cur = n & 1;
+        const int check = (n + 1) % kCheckEvery == 0 || n + 1 == nt;
+        if (warp == C::NCW) {   // producer: lane 0 waits and issues, the warp copies
+            constexpr int kWords = sizeof(ShotInfo) / 4;
+            if (lane == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+            TileRec next = blockIdx.x < bp.ntiles ? bp.tiles[blockIdx.x] : TileRec{};
+            for (int g = blockIdx.x; g < bp.ntiles; g += G, ++i) {
+                const int b = i % NB;
+                const TileRec rec = next;
+                if (g + G < bp.ntiles) next = bp.tiles[g + G];
+                int go = 1;
+                if (lane == 0) {
+                    if (i >= NB && !mbar_wait_bounded(&empty[b], (uint32_t)((i / NB - 1) & 1))) {
+                        atomicOr(bp.status, kStatusTimeout);
+                        *abort_v = 1;
+                    }
+                    go = !*abort_v;
+                }
+                if (!__shfl_sync(0xffffffffu, go, 0)) break;
+                const ShotDesc &d = bp.shots[rec.shot];
+                if (lane == 0) {
+                    float *fd = sm + b * C::SLOT;
+                    mbar_expect_tx(&full[b], BYTES);
+                    tma_load_2d(fd, &d.tmap[cur], &full[b], rec.x0 - C::HX, rec.z0 - M);
+                    tma_load_2d(fd + C::AEL, &d.tile[cur ^ 1], &full[b], rec.x0, rec.z0);
+                    tma_load_2d(fd + C::AEL + C::TEL, &d.ktile, &full[b], rec.x0, rec.z0);
+                    staged[b].rec = rec;
+                }
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(&d.info);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(&staged[b].info);
+                for (int k = lane; k < kWords; k += 32) dst[k] = src[k];
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();
+                    mbar_arrive(&full[b]);
+                }
+            }
+            if (lane == 0 && *abort_v) {   // let the copies in flight land before leaving
+                for (int j = i > NB ? i - NB : 0; j < i; ++j)
+                    mbar_wait_bounded(&full[j % NB], (j / NB) & 1, 100000000LL);
+            }
+        } else {
+            bool ok = true;
+            for (int g = blockIdx.x; g < bp.ntiles; g += G, ++i) {
+                const int b = i % NB;
+                if (*abort_v) break;
+                ok = mbar_wait_bounded(&full[b], (i / NB) & 1);
+                if (!ok) break;
+                const BatchView v(staged[b].info, bp, n, cur, check);
+                stream_tile<SHAPE, M, R, kModeForward>(v, staged[b], sm + b * C::SLOT, tx, ty);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[b]);
+            }
+            if (!ok) {
+                atomicOr(bp.status, kStatusTimeout);
+                *abort_v = 1;
+            }
+        }
+        if (!batch_grid_sync(bp, *abort_v != 0)) return;
     }
 }
 
@@ -1076,6 +1224,18 @@ cudaError_t launch_batched2d(const Variant &v, const BatchParams &bp, int ntiles
     return cudaGetLastError();
 }
 
+using BatchPFn = void (*)(const BatchParams, int);
+
+BatchPFn lookup_batched_persistent(int shape, int M, int R)
+{
+#define FDW_B(S, MM, RR) \
+    if (shape == S && M == MM && R == RR) return step2d_batched_persistent<S, MM, RR>;
+    FDW_B(FD_CROSS, 2, 2) FDW_B(FD_CROSS, 4, 2) FDW_B(FD_CROSS, 8, 2)
+    FDW_B(FD_CROSS, 2, 4) FDW_B(FD_CROSS, 4, 4) FDW_B(FD_CROSS, 8, 4)
+#undef FDW_B
+    return nullptr;
+}
+
 using Batch2Fn = void (*)(const BatchParams);
 
 Batch2Fn lookup_batched2(int shape, int M)
@@ -1125,6 +1285,28 @@ cudaError_t launch_batched2d2(const Variant &v, const BatchParams &bp, int ntile
     const int grid = std::min(ntiles, std::max(1, per_sm) * sms);
     fn<<<grid, kThreads + 32, smem, s>>>(bp);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batched2d_persistent(const Variant &v, const BatchParams &bp, int ntiles, int nt,
+                                       cudaStream_t s)
+{
+    BatchPFn fn = lookup_batched_persistent(v.shape, v.M, v.tz / kTZ);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+    if (e != cudaSuccess) return e;
+    if (ntiles <= 0 || nt <= 0) return cudaSuccess;
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev)) != cudaSuccess) return e;
+    if (!coop) return cudaErrorNotSupported;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, v.threads, v.smem)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = std::min(ntiles, per_sm * sms);   // all resident: the grid barrier needs it
+    void *args[] = {const_cast<BatchParams *>(&bp), &nt};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(fn), dim3(grid), dim3(v.threads), args,
+                                       v.smem, s);
 }
 
 int variants_2d(int shape, int M, int *r_out, int cap)

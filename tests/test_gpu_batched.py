@@ -43,7 +43,7 @@ def _shots(M=4, scheme="spatte", dim=2, nt=120):
     return cases
 
 
-def _batched(cases, repeat=1, rows=0, autotune=False):
+def _batched(cases, repeat=1, rows=0, autotune=False, status=None):
     import torch
     import paper_2606_04882_gb300 as F
     dev = torch.device("cuda")
@@ -67,6 +67,8 @@ def _batched(cases, repeat=1, rows=0, autotune=False):
         F.fd_forward_batched(shots, ws)
         torch.cuda.synchronize()
         outs.append([d["traces"].cpu().numpy() for d in shots])
+        if status is not None:   # shot 0's status word holds the batch's conditions
+            status.append(F.fd_status_read(shots[0]["plan"], ws))
     return outs
 
 
@@ -125,3 +127,25 @@ def test_batched_tile_shapes_and_autotune_keep_the_bits(M):
         for i in range(len(cases)):
             assert np.array_equal(outs[0][i], ref[i]), (kw, i)
             assert np.array_equal(outs[1][i], ref[i]), (kw, i)
+
+
+@pytest.mark.parametrize("M", [2, 4, 8])
+def test_batched_persistent_launch_keeps_the_bits(M, monkeypatch):
+    """With FDWAVE_BATCH_PERSISTENT=1 the batch runs every step in one
+    cooperative launch (a grid barrier between steps); traces equal the
+    single-shot runs bit for bit for both tile shapes, on a long, a ragged and a
+    one-step run, and the status word stays clear."""
+    for nt in (70, 33, 1):
+        cases = _shots(M, "spatte", nt=nt)
+        ref = [c.gpu_forward()[0] for c in cases]
+        monkeypatch.setenv("FDWAVE_BATCH_PERSISTENT", "1")
+        try:
+            for rows in (2, 4):
+                st = []
+                outs = _batched(cases, repeat=2, rows=rows, status=st)
+                assert st == [0, 0], (nt, rows, st)
+                for i in range(len(cases)):
+                    assert np.array_equal(outs[0][i], ref[i]), (nt, rows, i)
+                    assert np.array_equal(outs[1][i], ref[i]), (nt, rows, i)
+        finally:
+            monkeypatch.delenv("FDWAVE_BATCH_PERSISTENT")
