@@ -71,8 +71,8 @@ TRAFFIC_SOURCES = ("paper_2606_04882_gb300/csrc/step3d.cu",
                    "paper_2606_04882_gb300/csrc/step3d_common.cuh",
                    "paper_2606_04882_gb300/csrc/device_common.cuh",
                    "paper_2606_04882_gb300/csrc/internal.h")
-TRAFFIC_DIGEST = "67448eafb4897353668d2e5405ca7ccba9db0cceff205e4cc2e03a4842fde978"
-TRAFFIC_B_PER_POINT = {"cross4_spatte": 16.563, "cross8_spatte": 16.408, "rhombus4_displs": 16.592}
+TRAFFIC_DIGEST = "8ed9a4fb2b538024bbee57a856795013116aac6c7cdb8d2a1dceced3a09774a5"
+TRAFFIC_B_PER_POINT = {"cross4_spatte": 16.565, "cross8_spatte": 16.799, "rhombus4_displs": 16.475}
 
 
 def traffic_per_launch(stencil, pts):
