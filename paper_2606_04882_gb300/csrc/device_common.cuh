@@ -141,16 +141,19 @@ __device__ __forceinline__ float layer_d2(int64_t i, int64_t lo, int64_t hi)
     return __int2float_rn(d * d);
 }
 
-// Leapfrog bracket with explicit rounding (no contraction), so every kernel
-// mode (forward, forward + D store, adjoint) rounds identically:
-//   o = ((u - u_prev) + u) + kappa*lap + g*u_prev = 2u - (1-g)u_prev + kappa lap.
-// Returns D = kappa * lap.
+// Leapfrog bracket o = 2u - (1-g)u_prev + kappa lap, written as
+//   o = u + (kappa*lap + (g*u_prev + (u - u_prev)))
+// with explicit roundings and fused multiply-adds: the increment is formed at
+// its own (small) scale and meets u in one rounding, where ((u - u_prev) + u)
+// + kappa*lap rounds twice at the scale of u; over a long run that halves the
+// dominant rounding error.  Nothing is left for the code generator to contract,
+// so every kernel mode (forward, store-D, adjoint) rounds identically.
+// Returns D = kappa * lap (its own rounded product).
 __device__ __forceinline__ float step_update(float u, float up, float k, float lap, float g,
                                              float &o)
 {
-    const float d = __fmul_rn(k, lap);
-    o = __fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(u, up), u), d), __fmul_rn(g, up));
-    return d;
+    o = __fadd_rn(u, fmaf(k, lap, fmaf(g, up, __fsub_rn(u, up))));
+    return __fmul_rn(k, lap);
 }
 
 // ---------------------------------------------------------------------------
@@ -194,19 +197,33 @@ __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
     return r;
 }
 // float4 in shared memory as two packed pairs (x, y) and (z, w)
+// (w[i] + w[j], w[i+1] + w[j+1]) for a window w held in registers (i, j
+// compile-time after unrolling): one packed add when both pairs start on an
+// even element (an aligned register pair of the float4 they were loaded as),
+// else two scalar adds whose results the compiler places as a pair, instead of
+// moving misaligned operands into pairs first.  The same IEEE adds either way.
+__device__ __forceinline__ f32x2 pair_add(const float *w, int i, int j)
+{
+    if (((i | j) & 1) == 0) return add2(pk2(w[i], w[i + 1]), pk2(w[j], w[j + 1]));
+    return pk2(w[i] + w[j], w[i + 1] + w[j + 1]);
+}
+
 __device__ __forceinline__ void ld4x2(const float *p, f32x2 &a, f32x2 &b)
 {
     const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
     a = v.x;
     b = v.y;
 }
-// Packed form of step_update (same rounding, lane by lane).
+// Packed form of step_update (the same roundings, lane by lane).  The fused
+// multiply-adds are written out because a packed multiply whose only use is a
+// packed add may be fused by the code generator: a bracket written as separate
+// multiplies and adds would round differently in a kernel that also stores D
+// (a second use of the product) than in one that does not.
 __device__ __forceinline__ f32x2 step_update2(f32x2 u, f32x2 up, f32x2 k, f32x2 lap, f32x2 g,
                                               f32x2 &o)
 {
-    const f32x2 d = mul2(k, lap);
-    o = add2(add2(add2(sub2(u, up), u), d), mul2(g, up));
-    return d;
+    o = add2(u, fma2(k, lap, fma2(g, up, sub2(u, up))));
+    return mul2(k, lap);
 }
 
 __device__ __forceinline__ float4 ld4(const float *p)
@@ -224,12 +241,31 @@ __device__ __forceinline__ float get4(const float4 &v, int j)
     return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
 }
 
+// The scalar parts of the step (the sponge factor and division, the source
+// term added inside the bracket) use explicit rounding too, so that no
+// instantiation of a step kernel (mode, growth check) can contract them
+// differently from another: g = gcoef * d2, o / (1 + g), scale * series.
+__device__ __forceinline__ float sponge_g(float gcoef, float d2)
+{
+    return __fmul_rn(gcoef, d2);
+}
+
+__device__ __forceinline__ float sponge_div(float o, float g)
+{
+    return g != 0.f ? __fdividef(o, __fadd_rn(1.f, g)) : o;
+}
+
+__device__ __forceinline__ float src_term(float scale, float series)
+{
+    return __fmul_rn(scale, series);
+}
+
 __device__ __forceinline__ void add4(float4 &v, int j, float a)
 {
-    v.x += (j == 0) ? a : 0.f;
-    v.y += (j == 1) ? a : 0.f;
-    v.z += (j == 2) ? a : 0.f;
-    v.w += (j == 3) ? a : 0.f;
+    v.x = __fadd_rn(v.x, (j == 0) ? a : 0.f);
+    v.y = __fadd_rn(v.y, (j == 1) ? a : 0.f);
+    v.z = __fadd_rn(v.z, (j == 2) ? a : 0.f);
+    v.w = __fadd_rn(v.w, (j == 3) ? a : 0.f);
 }
 
 }  // namespace fdw

@@ -31,9 +31,11 @@ struct PtEntry {
     float scale;     // value factor
 };
 
-// Launch modes.  Forward and store-D run the same kernel instantiation (the
-// D store is a runtime branch on dseg_out), so the checkpointed recompute of
-// the gradient reproduces the forward sweep bitwise.
+// Launch modes.  The specialised 3D kernels instantiate each mode (the D store
+// is compile-time there); the 2D and generic kernels run forward and store-D
+// in one instantiation with a run-time branch on dseg_out.  Every mode does the
+// same arithmetic, so the checkpointed recompute of the gradient reproduces
+// the forward sweep bitwise.
 enum Mode : int {
     kModeForward = 0,     // plain step: inject sources, sample receivers
     kModeStoreD = 1,      // forward step that also writes D = kappa * lap to dseg_out

@@ -195,21 +195,21 @@ __device__ __forceinline__ void step2d_tile(const PP &p, const int tile, float *
         float o[4], dv[4], g[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            g[j] = p.gcoef * (d2x[j] + d2z);
+            g[j] = sponge_g(p.gcoef, d2x[j] + d2z);
             dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
         }
         // injection inside the bracket; adjoint residuals are scaled by kappa
         if (ib < ie)
             for_row(p.inj, ib, ie, zg, tx, [&](int j, const PtEntry &en) {
-                float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
-                if (MODE == kModeAdjoint) a *= kk[j];
+                float a = src_term(en.scale, p.inj_series[(int64_t)p.step * p.inj_ncol + en.col]);
+                if (MODE == kModeAdjoint) a = __fmul_rn(a, kk[j]);
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
-                    if (jj == j) o[jj] += a;
+                    if (jj == j) o[jj] = __fadd_rn(o[jj], a);
             });
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+            o[j] = sponge_div(o[j], g[j]);
         if (sb < se)
             for_row(p.smp, sb, se, zg, tx, [&](int j, const PtEntry &en) {
                 float v = 0.f;
@@ -343,20 +343,20 @@ __device__ __forceinline__ void stream_tile(const BatchView &v, const Staged &st
         float o[4], dv[4], g[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            g[j] = v.gcoef * (d2x[j] + d2z);
+            g[j] = sponge_g(v.gcoef, d2x[j] + d2z);
             dv[j] = step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
         }
         if (st.rec.ib < st.rec.ie)
             for_row(v.inj, st.rec.ib, st.rec.ie, zg, tx, [&](int j, const PtEntry &en) {
-                float a = en.scale * v.inj_series[(int64_t)v.step * v.inj_ncol + en.col];
-                if (MODE == kModeAdjoint) a *= kk[j];
+                float a = src_term(en.scale, v.inj_series[(int64_t)v.step * v.inj_ncol + en.col]);
+                if (MODE == kModeAdjoint) a = __fmul_rn(a, kk[j]);
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
-                    if (jj == j) o[jj] += a;
+                    if (jj == j) o[jj] = __fadd_rn(o[jj], a);
             });
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+            o[j] = sponge_div(o[j], g[j]);
         if (st.rec.sb < st.rec.se)
             for_row(v.smp, st.rec.sb, st.rec.se, zg, tx, [&](int j, const PtEntry &en) {
                 float s = 0.f;
@@ -692,21 +692,21 @@ __device__ __forceinline__ void stream2_tile(const BatchView &v, const Staged &s
         float o[4], g[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            g[j] = v.gcoef * (layer_d2(ex0 + c0 + j, v.phys_lo[0], v.phys_hi[0]) + d2z);
+            g[j] = sponge_g(v.gcoef, layer_d2(ex0 + c0 + j, v.phys_lo[0], v.phys_hi[0]) + d2z);
             step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
         }
         for (int k = st.rec.xb; k < st.rec.xe; ++k) {
             const PtEntry en = ext[k];
             const int xl = en.yx & 0xffff;
             if (en.z != zg || (xl >> 2) != gx) continue;
-            const float a = en.scale * v.inj_series[(int64_t)v.step * v.inj_ncol + en.col];
+            const float a = src_term(en.scale, v.inj_series[(int64_t)v.step * v.inj_ncol + en.col]);
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
-                if (jj == (xl & 3)) o[jj] += a;
+                if (jj == (xl & 3)) o[jj] = __fadd_rn(o[jj], a);
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+            o[j] = sponge_div(o[j], g[j]);
         *reinterpret_cast<float4 *>(u1 + rz * C::EW + c0) = make_float4(o[0], o[1], o[2], o[3]);
         // points of the tile itself: store and sample step n
         const int tr = rz - M, tc = c0 - C::HX;
@@ -749,21 +749,21 @@ __device__ __forceinline__ void stream2_tile(const BatchView &v, const Staged &s
         float o[4], g[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            g[j] = v.gcoef * (d2x[j] + d2z);
+            g[j] = sponge_g(v.gcoef, d2x[j] + d2z);
             step_update(cc[j], uu[j], kk[j], lap[j], g[j], o[j]);
         }
         for (int k = st.rec.xb; k < st.rec.xe; ++k) {
             const PtEntry en = ext[k];
             const int xl = (en.yx & 0xffff) - C::HX;
             if (en.z != zg || xl < 0 || (xl >> 2) != tx) continue;
-            const float a = en.scale * v.inj_series[(int64_t)step1 * v.inj_ncol + en.col];
+            const float a = src_term(en.scale, v.inj_series[(int64_t)step1 * v.inj_ncol + en.col]);
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
-                if (jj == (xl & 3)) o[jj] += a;
+                if (jj == (xl & 3)) o[jj] = __fadd_rn(o[jj], a);
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (g[j] != 0.f) o[j] = __fdividef(o[j], 1.f + g[j]);
+            o[j] = sponge_div(o[j], g[j]);
         if (st.rec.sb < st.rec.se)
             for_row(v.smp, st.rec.sb, st.rec.se, zg, tx, [&](int j, const PtEntry &en) {
                 float sv = 0.f;
@@ -1037,19 +1037,19 @@ __global__ void __launch_bounds__(kThreads) step2d_generic(const __grid_constant
             }
             lap += acc;
         }
-        gm[j] = p.gcoef * (layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2z);
+        gm[j] = sponge_g(p.gcoef, layer_d2(xg + j, p.phys_lo[0], p.phys_hi[0]) + d2z);
         dv[j] = step_update(c, uu[j], kk[j], lap, gm[j], o[j]);
     }
     float4 br = make_float4(o[0], o[1], o[2], o[3]);
     if (ib < ie)
         for_row(p.inj, ib, ie, zg, tx, [&](int j, const PtEntry &en) {
-            float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
-            if (MODE == kModeAdjoint) a *= kk[j];
+            float a = src_term(en.scale, p.inj_series[(int64_t)p.step * p.inj_ncol + en.col]);
+            if (MODE == kModeAdjoint) a = __fmul_rn(a, kk[j]);
             add4(br, j, a);
         });
     o[0] = br.x; o[1] = br.y; o[2] = br.z; o[3] = br.w;
     for (int j = 0; j < 4; ++j)
-        if (gm[j] != 0.f) o[j] = __fdividef(o[j], 1.f + gm[j]);
+        o[j] = sponge_div(o[j], gm[j]);
     const float4 un = make_float4(o[0], o[1], o[2], o[3]);
     if (sb < se)
         for_row(p.smp, sb, se, zg, tx, [&](int j, const PtEntry &en) {

@@ -48,7 +48,7 @@ struct CrossCfg {
     static constexpr int THREADS = 16 * TY + 32;
 };
 
-template <int M, int MODE, int TY>
+template <int M, int MODE, int TY, bool CHECK>
 __global__ void __launch_bounds__(CrossCfg<M, TY>::THREADS, CrossCfg<M, TY>::MINB)
 step3d_cross(const __grid_constant__ StepParams p)
 {
@@ -222,7 +222,7 @@ step3d_cross(const __grid_constant__ StepParams p)
                 const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
                 float g[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) g[j] = p.gcoef * (d2xy[j] + d2z);
+                for (int j = 0; j < 4; ++j) g[j] = sponge_g(p.gcoef, d2xy[j] + d2z);
                 f32x2 o01, o23;
                 const f32x2 dv01 = step_update2(qa[ic], up01, k01, l01, pk2(g[0], g[1]), o01);
                 const f32x2 dv23 = step_update2(qb[ic], up23, k23, l23, pk2(g[2], g[3]), o23);
@@ -238,10 +238,10 @@ step3d_cross(const __grid_constant__ StepParams p)
                     zinj = r.z;
                 }
                 if (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f || g[3] != 0.f) {
-                    o.x = g[0] != 0.f ? __fdividef(o.x, 1.f + g[0]) : o.x;
-                    o.y = g[1] != 0.f ? __fdividef(o.y, 1.f + g[1]) : o.y;
-                    o.z = g[2] != 0.f ? __fdividef(o.z, 1.f + g[2]) : o.z;
-                    o.w = g[3] != 0.f ? __fdividef(o.w, 1.f + g[3]) : o.w;
+                    o.x = sponge_div(o.x, g[0]);
+                    o.y = sponge_div(o.y, g[1]);
+                    o.z = sponge_div(o.z, g[2]);
+                    o.w = sponge_div(o.w, g[3]);
                 }
                 if (z >= zsmp) {
                     const int2 r = sample_plane<MODE>(p, ks, kse, z, tx, ty, o, kk);
@@ -250,9 +250,9 @@ step3d_cross(const __grid_constant__ StepParams p)
                 }
                 if (colok) {
                     const int64_t off = (int64_t)z * p.plane + colo;
-                    if (p.check) check_growth(p.status, o);
+                    if (CHECK) check_growth(p.status, o);
                     *reinterpret_cast<float4 *>(p.u_prev + off) = o;
-                    if (MODE != kModeAdjoint && p.dseg_out)
+                    if (MODE == kModeStoreD)
                         *reinterpret_cast<ulonglong2 *>(p.dseg_out + off) = make_ulonglong2(dv01, dv23);
                     if (MODE == kModeAdjoint) {
                         const float4 dd = ldg4(p.dseg_in + off);
@@ -293,7 +293,7 @@ struct PlanarCfg {
     static constexpr int THREADS = 16 * TY + 32;
 };
 
-template <int SHAPE, int M, int MODE, int TY>
+template <int SHAPE, int M, int MODE, int TY, bool CHECK>
 __global__ void __launch_bounds__(PlanarCfg<M, TY>::THREADS, PlanarCfg<M, TY>::MINB)
 step3d_planar(const __grid_constant__ StepParams p)
 {
@@ -449,8 +449,7 @@ step3d_planar(const __grid_constant__ StepParams p)
                     f32x2 ps[M + 1];
 #pragma unroll
                     for (int pp = 1; pp <= M; ++pp)
-                        ps[pp] = sub2(add2(pk2(win[b + pp], win[b + pp + 1]),
-                                           pk2(win[b - pp], win[b - pp + 1])), u2[h]);
+                        ps[pp] = sub2(pair_add(win, b + pp, b - pp), u2[h]);
 #pragma unroll
                     for (int s = 0; s <= M; ++s) {
                         const int E = shape_ext(SHAPE, M, 0, s);
@@ -485,9 +484,7 @@ step3d_planar(const __grid_constant__ StepParams p)
                     f32x2 a = mul2(p.w2[q], d0);
 #pragma unroll
                     for (int pp = 1; pp <= E; ++pp)
-                        a = fma2(p.w2[pp * kW3 + q],
-                                 sub2(add2(pk2(win[b + pp], win[b + pp + 1]),
-                                           pk2(win[b - pp], win[b - pp + 1])), u4[h]), a);
+                        a = fma2(p.w2[pp * kW3 + q], sub2(pair_add(win, b + pp, b - pp), u4[h]), a);
                     T[0][h] = add2(T[0][h], a);
 #pragma unroll
                     for (int s = 1; s <= M; ++s)
@@ -527,7 +524,7 @@ step3d_planar(const __grid_constant__ StepParams p)
             const float d2z = layer_d2(z, p.phys_lo[2], p.phys_hi[2]);
             float g[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) g[j] = p.gcoef * (d2xy[j] + d2z);
+            for (int j = 0; j < 4; ++j) g[j] = sponge_g(p.gcoef, d2xy[j] + d2z);
             f32x2 o01, o23;
             const f32x2 dv01 = step_update2(pk2(cv.x, cv.y), pk2(upv.x, upv.y), pk2(kpv.x, kpv.y),
                                             acc[uu][0], pk2(g[0], g[1]), o01);
@@ -543,10 +540,10 @@ step3d_planar(const __grid_constant__ StepParams p)
                 zinj = r.z;
             }
             if (g[0] != 0.f || g[1] != 0.f || g[2] != 0.f || g[3] != 0.f) {
-                o.x = g[0] != 0.f ? __fdividef(o.x, 1.f + g[0]) : o.x;
-                o.y = g[1] != 0.f ? __fdividef(o.y, 1.f + g[1]) : o.y;
-                o.z = g[2] != 0.f ? __fdividef(o.z, 1.f + g[2]) : o.z;
-                o.w = g[3] != 0.f ? __fdividef(o.w, 1.f + g[3]) : o.w;
+                o.x = sponge_div(o.x, g[0]);
+                o.y = sponge_div(o.y, g[1]);
+                o.z = sponge_div(o.z, g[2]);
+                o.w = sponge_div(o.w, g[3]);
             }
             if (z >= zsmp) {
                 const int2 r = sample_plane<MODE>(p, ks, kse, z, tx, ty, o, kpv);
@@ -555,9 +552,9 @@ step3d_planar(const __grid_constant__ StepParams p)
             }
             if (colok) {
                 const int64_t off = (int64_t)z * p.plane + colo;
-                if (p.check) check_growth(p.status, o);
+                if (CHECK) check_growth(p.status, o);
                 *reinterpret_cast<float4 *>(p.u_prev + off) = o;
-                if (MODE != kModeAdjoint && p.dseg_out)
+                if (MODE == kModeStoreD)
                     *reinterpret_cast<ulonglong2 *>(p.dseg_out + off) = make_ulonglong2(dv01, dv23);
                 if (MODE == kModeAdjoint) {
                     const float4 dd = ldg4(p.dseg_in + off);
@@ -664,7 +661,7 @@ __global__ void __launch_bounds__(16 * kGenTY) step3d_generic(const __grid_const
         float o[4], dv[4], g[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            g[j] = p.gcoef * (d2xy[j] + d2z);
+            g[j] = sponge_g(p.gcoef, d2xy[j] + d2z);
             dv[j] = step_update(cc[j], upa[j], ka[j], lap[j], g[j], o[j]);
         }
         float4 of = make_float4(o[0], o[1], o[2], o[3]);
@@ -674,10 +671,10 @@ __global__ void __launch_bounds__(16 * kGenTY) step3d_generic(const __grid_const
             ki = r.k;
             zinj = r.z;
         }
-        of.x = g[0] != 0.f ? __fdividef(of.x, 1.f + g[0]) : of.x;
-        of.y = g[1] != 0.f ? __fdividef(of.y, 1.f + g[1]) : of.y;
-        of.z = g[2] != 0.f ? __fdividef(of.z, 1.f + g[2]) : of.z;
-        of.w = g[3] != 0.f ? __fdividef(of.w, 1.f + g[3]) : of.w;
+        of.x = sponge_div(of.x, g[0]);
+        of.y = sponge_div(of.y, g[1]);
+        of.z = sponge_div(of.z, g[2]);
+        of.w = sponge_div(of.w, g[3]);
         if (z >= zsmp) {
             const int2 r = sample_plane<MODE>(p, ks, kse, z, tx, ty, of, kk);
             ks = r.x;
@@ -698,35 +695,51 @@ __global__ void __launch_bounds__(16 * kGenTY) step3d_generic(const __grid_const
     }
 }
 
-template <int SHAPE, int M, int TY>
-KernelFn pick_planar(int mode)
+// The growth check and the D store are template parameters (the check flag
+// and the mode): run-time tests of p.check and p.dseg_out in the store loop
+// measured 1-4 % and 1-3 % slower on every step.  The checked instantiation
+// runs only on the steps that check (one in kCheckEvery and the last).  The
+// three modes share their arithmetic, every operation of which is explicitly
+// rounded (nothing the compiler may contract differently in one
+// instantiation), so the store-D recompute reproduces the forward sweep bit
+// for bit.
+template <int SHAPE, int M, int TY, int MODE>
+KernelFn pick_planar_m(bool check)
 {
-    switch (mode) {
-    case kModeForward: return step3d_planar<SHAPE, M, kModeForward, TY>;
-    case kModeStoreD: return step3d_planar<SHAPE, M, kModeForward, TY>;
-    default: return step3d_planar<SHAPE, M, kModeAdjoint, TY>;
-    }
+    return check ? step3d_planar<SHAPE, M, MODE, TY, true> : step3d_planar<SHAPE, M, MODE, TY, false>;
+}
+
+template <int SHAPE, int M, int TY>
+KernelFn pick_planar(int mode, bool check)
+{
+    if (mode == kModeAdjoint) return pick_planar_m<SHAPE, M, TY, kModeAdjoint>(check);
+    if (mode == kModeStoreD) return pick_planar_m<SHAPE, M, TY, kModeStoreD>(check);
+    return pick_planar_m<SHAPE, M, TY, kModeForward>(check);
+}
+
+template <int M, int TY, int MODE>
+KernelFn pick_cross_m(bool check)
+{
+    return check ? step3d_cross<M, MODE, TY, true> : step3d_cross<M, MODE, TY, false>;
 }
 
 template <int M, int TY>
-KernelFn pick_cross(int mode)
+KernelFn pick_cross(int mode, bool check)
 {
-    switch (mode) {
-    case kModeForward: return step3d_cross<M, kModeForward, TY>;
-    case kModeStoreD: return step3d_cross<M, kModeForward, TY>;
-    default: return step3d_cross<M, kModeAdjoint, TY>;
-    }
+    if (mode == kModeAdjoint) return pick_cross_m<M, TY, kModeAdjoint>(check);
+    if (mode == kModeStoreD) return pick_cross_m<M, TY, kModeStoreD>(check);
+    return pick_cross_m<M, TY, kModeForward>(check);
 }
 
-KernelFn lookup3(int shape, int M, int ty, int mode)
+KernelFn lookup3(int shape, int M, int ty, int mode, bool check = false)
 {
 #define FDW_Q(MM, TT) \
-    if (shape == FD_CROSS && M == MM && ty == TT) return pick_cross<MM, TT>(mode);
+    if (shape == FD_CROSS && M == MM && ty == TT) return pick_cross<MM, TT>(mode, check);
     FDW_Q(1, 16) FDW_Q(2, 16) FDW_Q(3, 16) FDW_Q(4, 16) FDW_Q(6, 8) FDW_Q(8, 8)
     FDW_Q(2, 8) FDW_Q(4, 8)
 #undef FDW_Q
 #define FDW_P(S, MM, TT) \
-    if (shape == S && M == MM && ty == TT) return pick_planar<S, MM, TT>(mode);
+    if (shape == S && M == MM && ty == TT) return pick_planar<S, MM, TT>(mode, check);
     FDW_P(FD_RHOMBUS, 2, 16) FDW_P(FD_RHOMBUS, 3, 16) FDW_P(FD_RHOMBUS, 4, 16)
     FDW_P(FD_RHOMBUS, 6, 8) FDW_P(FD_RHOMBUS, 8, 8) FDW_P(FD_SQUARE, 2, 16) FDW_P(FD_SQUARE, 4, 16)
     FDW_P(FD_RHOMBUS, 4, 8)
@@ -814,7 +827,7 @@ cudaError_t launch_step3d(const Variant &v, int mode, const StepParams &p, cudaS
         gfn<<<grid, v.threads, 0, s>>>(p, v.shape, v.M, v.N);
         return cudaGetLastError();
     }
-    KernelFn fn = lookup3(v.shape, v.M, v.tz, mode);
+    KernelFn fn = lookup3(v.shape, v.M, v.tz, mode, p.check != 0);
     if (!fn) return cudaErrorInvalidValue;
     cudaError_t e =
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);

@@ -77,8 +77,8 @@ __device__ __noinline__ InjOut inject_plane(const StepParams &p, int k, int kend
                                             int ty, float4 o, float4 kk)
 {
     plane_entries(p.inj, k, kend, z, tx, ty, [&](int j, const PtEntry &en) {
-        float a = en.scale * p.inj_series[(int64_t)p.step * p.inj_ncol + en.col];
-        if (MODE == kModeAdjoint) a *= get4(kk, j);
+        float a = src_term(en.scale, p.inj_series[(int64_t)p.step * p.inj_ncol + en.col]);
+        if (MODE == kModeAdjoint) a = __fmul_rn(a, get4(kk, j));
         add4(o, j, a);
     });
     InjOut r;
