@@ -71,8 +71,8 @@ TRAFFIC_SOURCES = ("paper_2606_04882_gb300/csrc/step3d.cu",
                    "paper_2606_04882_gb300/csrc/step3d_common.cuh",
                    "paper_2606_04882_gb300/csrc/device_common.cuh",
                    "paper_2606_04882_gb300/csrc/internal.h")
-TRAFFIC_DIGEST = "8ed9a4fb2b538024bbee57a856795013116aac6c7cdb8d2a1dceced3a09774a5"
-TRAFFIC_B_PER_POINT = {"cross4_spatte": 16.565, "cross8_spatte": 16.799, "rhombus4_displs": 16.475}
+TRAFFIC_DIGEST = "95e7de9d5193cf40d9dcda1f425990604bde9375410da6f0cd481c6f3653bb3a"
+TRAFFIC_B_PER_POINT = {"cross4_spatte": 16.487, "cross8_spatte": 16.776, "rhombus4_displs": 16.485}
 
 
 def traffic_per_launch(stencil, pts):
