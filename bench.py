@@ -696,6 +696,25 @@ def run_metrics(args):
     print(json.dumps(out))
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name on x86; implementer
+    and part numbers on Arm, e.g. 0x41/0xd4f for a Neoverse V2)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    kv = {}
+    for ln in info:
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            kv.setdefault(k.strip().lower(), v.strip())
+    if "model name" in kv:
+        return kv["model name"]
+    if "cpu implementer" in kv:
+        return "Arm implementer %s part %s" % (kv["cpu implementer"], kv.get("cpu part", "?"))
+    return "unknown"
+
+
 def cpu_baseline(pr, dt, steps=2):
     """The FP64 oracle on a bounded sample: `steps` time steps of the full
     460^3 grid with the Cross(4) stencil on all host cores."""
@@ -709,7 +728,7 @@ def cpu_baseline(pr, dt, steps=2):
     el = time.perf_counter() - t
     pts = int(np.prod(st.pshape))
     return {"value": pts * steps / el / 1e9, "unit": "Gpts/s", "cores": threads, "kind": "oracle",
-            "sample": "%d time steps of the %d^3 padded grid, Cross(4), FP64 C oracle" % (steps, st.pshape[0])}
+            "cpu": cpu_model(), "sample": "%d time steps of the %d^3 padded grid, Cross(4), FP64 C oracle" % (steps, st.pshape[0])}
 
 
 def run_reference(args):
@@ -748,7 +767,7 @@ def run_reference(args):
                                   % (args.n, setups[0].pshape[0], args.nt,
                                      ",".join("%s%d_%s" % st for st in STENCILS))},
            "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": threads, "kind": "oracle",
-                            "sample": "one time step of the full padded grid per bench step, "
+                            "cpu": cpu_model(), "sample": "one time step of the full padded grid per bench step, "
                                       "cycling through the three stencils"},
            "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
