@@ -68,10 +68,12 @@ def dist_env():
 # scaled to the bench grid by its point count), valid only for the kernel
 # sources whose digest is recorded with them.
 TRAFFIC_SOURCES = ("paper_2606_04882_gb300/csrc/step3d.cu",
+                   "paper_2606_04882_gb300/csrc/step3d_cross.cu",
+                   "paper_2606_04882_gb300/csrc/step3d_planar.cu",
                    "paper_2606_04882_gb300/csrc/step3d_common.cuh",
                    "paper_2606_04882_gb300/csrc/device_common.cuh",
                    "paper_2606_04882_gb300/csrc/internal.h")
-TRAFFIC_DIGEST = "95e7de9d5193cf40d9dcda1f425990604bde9375410da6f0cd481c6f3653bb3a"
+TRAFFIC_DIGEST = "50d1f10be7ca390c5f97e54fd4550e088068405780c0a2f9f8045b10ecbfd251"
 TRAFFIC_B_PER_POINT = {"cross4_spatte": 16.487, "cross8_spatte": 16.776, "rhombus4_displs": 16.485}
 
 

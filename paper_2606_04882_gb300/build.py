@@ -18,7 +18,8 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["weights.cpp", "plan.cu", "aux.cu", "step2d.cu", "step3d.cu", "noalloc.cu", "metrics.cu"]
+SOURCES = ["step3d_cross.cu", "step3d_planar.cu", "step2d.cu", "step3d.cu", "plan.cu", "weights.cpp",
+           "aux.cu", "noalloc.cu", "metrics.cu"]   # longest compiles first
 
 
 def _deps_mtime() -> float:

@@ -103,4 +103,11 @@ __device__ __noinline__ int2 sample_plane(const StepParams &p, int k, int kend, 
 using KernelFn = void (*)(const StepParams);
 
 }  // namespace
+
+// Instantiation lookups of the specialised kernels (step3d_cross.cu,
+// step3d_planar.cu): the kernel for a shape, radius, tile row count, mode and
+// growth check, or nullptr where none is built.
+KernelFn lookup_cross3(int M, int ty, int mode, bool check);
+KernelFn lookup_planar3(int shape, int M, int ty, int mode, bool check);
+
 }  // namespace fdw
