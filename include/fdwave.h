@@ -304,14 +304,17 @@ int fd_adjoint_gradient(fd_plan *plan, int model_kind, const float *model_d,
 /*
  * Batched shots (no counterpart in the paper, whose experiments run one
  * source at a time): independent forward problems, possibly on grids of
- * different size, with the same stencil, dt and nt, advanced together.  For 2D cross stencils with M = 2, 4, 8 each time step is
- * one launch of persistent CTAs over a table of every shot's tiles; other
+ * different size, with the same stencil, dt and nt, advanced together.  For
+ * 2D cross stencils with M = 2, 4, 8 each time step is one launch of
+ * persistent CTAs over a table of every shot's tiles; other
  * batches launch each shot's step kernel in turn.  The whole time loop is
  * captured once into a CUDA graph and replayed on repeat calls.  Fields of
  * every shot must fit the workspace at once.  With the environment variable
  * FDWAVE_BATCH_2STEP=1, Cross(2) and Cross(4) batches advance two time steps
  * per pass instead (temporal blocking; two more fields per shot in the
- * workspace, same results bit for bit).
+ * workspace, same results bit for bit).  With FDWAVE_BATCH_PERSISTENT=1, a
+ * single-launch batch runs all nt steps in one cooperative launch, with a
+ * bounded grid barrier between steps (same results bit for bit).
  * fd_forward_batched: traces only (no final states).  Errors: FD_ERR_ARG
  * (shots that differ in dim, stencil, dt or nt), FD_ERR_NOMEM, FD_ERR_CUDA.
  */
