@@ -368,6 +368,7 @@ def bench_gradient(args, dev, stream, peak, peak_kind, world):
     torch.cuda.synchronize()
     ems = a.elapsed_time(b) / len(shots)
     assert F.fd_status_read(plan, ws) == 0, F.last_error()
+    keep = keep_all_d(plan, pr, m, shots, wav, ri, resid, grad, stream, peak, peak_kind, pts)
     if world > 1:
         t = torch.tensor([ms, ems], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -386,7 +387,52 @@ def bench_gradient(args, dev, stream, peak, peak_kind, world):
                                  "restore 32/k, D store and load 8, gradient accumulator 8"},
             "e2e": {"value": work / (ems * 1e-3) / 1e9, "unit": "Gpts/s",
                     "h2d_bytes_per_step": m.numel() * 4, "d2h_bytes_per_step": grad.numel() * 4},
-            "gpu_launches": len(shots) * (3 * pr.nt + 2)}
+            "gpu_launches": len(shots) * (3 * pr.nt + 2), "keep_all_d": keep}
+
+
+KEEP_BYTES_PER_POINT = 2 * 16 + 8 + 8
+
+
+def keep_all_d(plan, pr, m, shots, wav, ri, resid, grad_k, stream, peak, peak_kind, pts):
+    """The same gradient with ckpt_every = nt: D of all 1200 steps stays in HBM
+    (about 124 GB), so the forward sweep stores D and nothing is recomputed.
+    Timed like the checkpointed run when the GPU has the room (else null); the
+    last shot's gradient is compared bit for bit with the checkpointed one."""
+    import torch
+    import paper_2606_04882_gb300 as F
+    need = plan.gradient_workspace_size(1, len(ri), pr.nt)
+    free, _ = torch.cuda.mem_get_info()
+    if need + (4 << 30) > free:
+        return None
+    ws = F.workspace(need, m.device)
+    g = torch.empty_like(grad_k)
+
+    def shot(si):
+        F.fd_adjoint_gradient(plan, m, si, wav, ri, resid, pr.nt, g, ws,
+                              model_kind=F.FD_MODEL_SLOWNESS2)
+
+    shot(shots[0])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for si in shots:
+        shot(si)
+    b.record(stream)
+    torch.cuda.synchronize()
+    assert F.fd_status_read(plan, ws) == 0, F.last_error()
+    ms = a.elapsed_time(b) / len(shots)
+    gbs = KEEP_BYTES_PER_POINT * pts * pr.nt / (ms * 1e-3) / 1e9
+    out = {"value": pts * pr.nt / (ms * 1e-3) / 1e9, "unit": "Gpts/s", "ms_per_shot": ms,
+           "workspace_gb": need / 1e9, "bitwise_equal_to_checkpointed": bool(torch.equal(g, grad_k)),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                        "frac": gbs / peak, "peak_source": peak_kind,
+                        "bytes_per_point": KEEP_BYTES_PER_POINT,
+                        "note": "forward sweep storing D (16 + 4 B) and adjoint sweep (16 B, D load "
+                                "4 B, gradient accumulator 8 B) per padded point and time step"},
+           "gpu_launches": len(shots) * (2 * pr.nt + 2)}
+    del ws
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_other(args):

@@ -285,7 +285,10 @@ int fd_status_read(const fd_plan *plan, void *ws_d, void *stream);
  *   resid_d     [nt][nrec] dJ/dtrace (for J = 1/2 ||d - d_obs||^2: d - d_obs)
  *   ckpt_every  k >= 1: the forward sweep stores (u^n, u^{n-1}) every k steps;
  *               the backward sweep recomputes each segment of k steps and runs
- *               the adjoint steps over it
+ *               the adjoint steps over it.  k >= nt keeps the D field of every
+ *               step (nt fields, e.g. 124 GB for 296^3 x 1200 steps): the
+ *               forward sweep stores D itself, with no checkpoint and no
+ *               recompute.  The gradient is bitwise the same for every k.
  *   grad_d      out physical [nz][ny][nx] dJ/dm (overwritten)
  *   traces_d    optional out [nt][nrec] traces of the forward sweep (NULL: none)
  *   wavelet_grad_d  optional out [nt][nsrc] dJ/ds(t^n) for each source, the

@@ -1049,11 +1049,17 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
         sp.smp_out = traces;
         sp.smp_ncol = nrec;
     };
+    // One segment (k >= nt: D of every step fits the workspace, e.g. 124 GB for
+    // 296^3 x 1200 steps): the forward sweep itself stores D, and there is no
+    // checkpoint and no recompute (48 instead of 64 + 32/k bytes per point and
+    // step).  The store-D mode rounds exactly like the forward mode, so the
+    // result is bitwise that of any checkpoint interval.
+    const bool store_all = L.nck == 1;
     // forward sweep with checkpoints (u^n, u^{n-1}) at n = s k
     bind_fwd(true);
     for (int n = 0; n < nt; ++n) {
         const int cur = n & 1;
-        if (n % k == 0) {
+        if (n % k == 0 && !store_all) {
             const int c = n / k;
             FDW_CK(cudaMemcpyAsync(ck + (size_t)(2 * c) * fb, buf[cur], fb, cudaMemcpyDeviceToDevice, s));
             FDW_CK(cudaMemcpyAsync(ck + (size_t)(2 * c + 1) * fb, buf[cur ^ 1], fb, cudaMemcpyDeviceToDevice, s));
@@ -1063,24 +1069,28 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
         sp.u_prev = buf[cur ^ 1];
         sp.step = n;
         sp.check = check_step(n, nt);
-        FDW_CK(launch(p, kModeForward, sp, s));
+        sp.dseg_out = store_all ? reinterpret_cast<float *>(dseg + (size_t)n * fb) : nullptr;
+        FDW_CK(launch(p, store_all ? kModeStoreD : kModeForward, sp, s));
     }
+    sp.dseg_out = nullptr;
     // backward sweep over segments
     int t = 0;   // adjoint steps done: q^{j+1} lives in buf[2 + (t & 1)]
     for (int c = L.nck - 1; c >= 0; --c) {
         const int k0 = c * k, k1 = std::min(k0 + k, nt);
-        FDW_CK(cudaMemcpyAsync(buf[0], ck + (size_t)(2 * c) * fb, fb, cudaMemcpyDeviceToDevice, s));
-        FDW_CK(cudaMemcpyAsync(buf[1], ck + (size_t)(2 * c + 1) * fb, fb, cudaMemcpyDeviceToDevice, s));
         bind_fwd(false);
-        for (int n = k0; n < k1; ++n) {
-            const int cur = (n - k0) & 1;
-            bind_maps(sp, maps, 4, cur, cur ^ 1);
-            sp.u_cur = buf[cur];
-            sp.u_prev = buf[cur ^ 1];
-            sp.step = n;
-            sp.check = 0;   // the recompute repeats the checked forward sweep bit for bit
-            sp.dseg_out = reinterpret_cast<float *>(dseg + (size_t)(n - k0) * fb);
-            FDW_CK(launch(p, kModeStoreD, sp, s));
+        if (!store_all) {
+            FDW_CK(cudaMemcpyAsync(buf[0], ck + (size_t)(2 * c) * fb, fb, cudaMemcpyDeviceToDevice, s));
+            FDW_CK(cudaMemcpyAsync(buf[1], ck + (size_t)(2 * c + 1) * fb, fb, cudaMemcpyDeviceToDevice, s));
+            for (int n = k0; n < k1; ++n) {
+                const int cur = (n - k0) & 1;
+                bind_maps(sp, maps, 4, cur, cur ^ 1);
+                sp.u_cur = buf[cur];
+                sp.u_prev = buf[cur ^ 1];
+                sp.step = n;
+                sp.check = 0;   // the recompute repeats the checked forward sweep bit for bit
+                sp.dseg_out = reinterpret_cast<float *>(dseg + (size_t)(n - k0) * fb);
+                FDW_CK(launch(p, kModeStoreD, sp, s));
+            }
         }
         sp.dseg_out = nullptr;
         sp.inj_ptr = nrec ? reinterpret_cast<const int32_t *>(w + L.tab + T.ainj_ptr) : nullptr;

@@ -154,6 +154,12 @@ def test_fwi_256_dot_product_and_checkpoint_invariance():
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
     g40, _ = _gpu_grad(c, d, 40, wavelet=s)
     assert np.array_equal(g20, g40)
+    # k = nt: D of every step resident (~124 GB), no checkpoint and no recompute
+    plan = c.plan()
+    torch.cuda.empty_cache()
+    if plan.gradient_workspace_size(1, len(c.rec), c.nt) + (8 << 30) < torch.cuda.mem_get_info()[0]:
+        g_all, _ = _gpu_grad(c, d, c.nt, wavelet=s)
+        assert np.array_equal(g20, g_all)
 
 
 def test_fwi_256_gradient_matches_oracle_on_full_grid():
