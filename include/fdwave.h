@@ -364,7 +364,8 @@ int fd_forward_batched_set_variant(int nshots, const fd_shot *shots, int rows);
  * M = 2, 4 or 8 every time step of each sweep is one launch of persistent
  * CTAs over the tiles of every shot; other batches run the shots one after
  * another.  Each shot's gradient (and traces) are bit for bit those of
- * fd_adjoint_gradient with the same ckpt_every.  Workspace: every shot's
+ * fd_adjoint_gradient with the same ckpt_every (and so with any ckpt_every;
+ * ckpt_every >= nt keeps every D and recomputes nothing).  Workspace: every shot's
  * gradient workspace plus the batch's tables.  Device status: the first
  * shot's status word (fd_status_read with the first plan and ws_d).
  * Errors: FD_ERR_ARG (shots that differ in dim, stencil, dt or nt, missing

@@ -1880,12 +1880,15 @@ extern "C" int fd_adjoint_gradient_batched(int nshots, const fd_grad_shot *shots
     const TileRec *trf = reinterpret_cast<const TileRec *>(xr);
     const TileRec *trr = reinterpret_cast<const TileRec *>(xr + rb);
     const TileRec *tra = reinterpret_cast<const TileRec *>(xr + 2 * rb);
-    // forward sweep with checkpoints (u^n, u^{n-1}) at n = c k
+    // forward sweep with checkpoints (u^n, u^{n-1}) at n = c k; with one
+    // segment (k >= nt) it stores D of every step instead, as in
+    // fd_adjoint_gradient, and the backward sweep recomputes nothing
+    const bool store_all = nck == 1;
     bp.shots = dfd;
     bp.tiles = trf;
     for (int n = 0; n < nt; ++n) {
         const int cur = n & 1;
-        if (n % k == 0)
+        if (n % k == 0 && !store_all)
             for (int i = 0; i < nshots; ++i) {
                 const int c = n / k;
                 FDW_CK(cudaMemcpyAsync(sb[i].ckpt + (size_t)(2 * c) * sb[i].fb, sb[i].buf[cur], sb[i].fb,
@@ -1895,28 +1898,30 @@ extern "C" int fd_adjoint_gradient_batched(int nshots, const fd_grad_shot *shots
             }
         bp.step = n;
         bp.parity = cur;
-        bp.seg = 0;
+        bp.seg = store_all ? n : 0;
         bp.check = check_step(n, nt);
-        FDW_CK(launch_batched2d(bv, bp, (int)ntiles_all, s, kModeForward));
+        FDW_CK(launch_batched2d(bv, bp, (int)ntiles_all, s, store_all ? kModeStoreD : kModeForward));
     }
     // backward sweep over segments: restore, recompute storing D, adjoint steps
     int t = 0;
     for (int c = nck - 1; c >= 0; --c) {
         const int k0 = c * k, k1 = std::min(k0 + k, nt);
-        for (int i = 0; i < nshots; ++i) {
-            FDW_CK(cudaMemcpyAsync(sb[i].buf[0], sb[i].ckpt + (size_t)(2 * c) * sb[i].fb, sb[i].fb,
-                                   cudaMemcpyDeviceToDevice, s));
-            FDW_CK(cudaMemcpyAsync(sb[i].buf[1], sb[i].ckpt + (size_t)(2 * c + 1) * sb[i].fb, sb[i].fb,
-                                   cudaMemcpyDeviceToDevice, s));
-        }
-        bp.shots = dfd;
-        bp.tiles = trr;
-        bp.check = 0;   // the recompute repeats the checked forward sweep bit for bit
-        for (int n = k0; n < k1; ++n) {
-            bp.step = n;
-            bp.parity = (n - k0) & 1;
-            bp.seg = n - k0;
-            FDW_CK(launch_batched2d(bv, bp, (int)ntiles_all, s, kModeStoreD));
+        if (!store_all) {
+            for (int i = 0; i < nshots; ++i) {
+                FDW_CK(cudaMemcpyAsync(sb[i].buf[0], sb[i].ckpt + (size_t)(2 * c) * sb[i].fb, sb[i].fb,
+                                       cudaMemcpyDeviceToDevice, s));
+                FDW_CK(cudaMemcpyAsync(sb[i].buf[1], sb[i].ckpt + (size_t)(2 * c + 1) * sb[i].fb, sb[i].fb,
+                                       cudaMemcpyDeviceToDevice, s));
+            }
+            bp.shots = dfd;
+            bp.tiles = trr;
+            bp.check = 0;   // the recompute repeats the checked forward sweep bit for bit
+            for (int n = k0; n < k1; ++n) {
+                bp.step = n;
+                bp.parity = (n - k0) & 1;
+                bp.seg = n - k0;
+                FDW_CK(launch_batched2d(bv, bp, (int)ntiles_all, s, kModeStoreD));
+            }
         }
         bp.shots = dad;
         bp.tiles = tra;

@@ -96,9 +96,12 @@ def test_checkpoint_interval_is_bitwise_invariant(dim, shape):
     store-D and adjoint sweeps run different kernel instantiations)."""
     c = _case(dim, 90 if dim == 2 else 70, shape=shape)
     resid = np.random.default_rng(4).standard_normal((c.nt, len(c.rec)))
-    g1 = _gpu_gradient(c, resid, k=1)[0]
-    for k in (7, 30, 90, 500):
-        assert np.array_equal(g1, _gpu_gradient(c, resid, k=k)[0]), k
+    g1, tr1, wg1, _ = _gpu_gradient(c, resid, k=1)
+    for k in (7, 30, 90, 500):   # k >= nt keeps every D and recomputes nothing
+        g, tr, wg, rc = _gpu_gradient(c, resid, k=k)
+        assert rc == 0
+        assert np.array_equal(g1, g), k
+        assert np.array_equal(tr1, tr) and np.array_equal(wg1, wg), k
 
 
 def test_slowness_parameterisation_and_autograd():
@@ -222,6 +225,17 @@ def test_batched_gradient_equals_per_shot_gradients(shape, M, scheme, rows):
         F.fd_forward_batched_set_variant(shots, rows)
     ws = F.workspace(F.batched_gradient_workspace_size(shots, k))
     F.fd_adjoint_gradient_batched(shots, k, ws)
+    assert F.fd_status_read(shots[0]["plan"], ws) == 0
+    for d, (g1, tr1, _, _) in zip(shots, ref):
+        assert np.array_equal(d["grad"].cpu().numpy(), g1)
+        assert np.array_equal(d["traces"].cpu().numpy(), tr1)
+    # ckpt_every >= nt: every shot's D kept, no checkpoint and no recompute, the same bits
+    del ws
+    ws = F.workspace(F.batched_gradient_workspace_size(shots, nt))
+    for d in shots:
+        d["grad"].fill_(float("nan"))
+        d["traces"].fill_(float("nan"))
+    F.fd_adjoint_gradient_batched(shots, nt, ws)
     assert F.fd_status_read(shots[0]["plan"], ws) == 0
     for d, (g1, tr1, _, _) in zip(shots, ref):
         assert np.array_equal(d["grad"].cpu().numpy(), g1)
