@@ -665,6 +665,18 @@ def batched_vs_single(args, dev, stream, shots, grad_shots=8, k=GRAD_K):
                                   d["resid"], k, d["grad"], w)
     gms_s = best(single_grad)
     same_grad = all(torch.equal(a, d["grad"]) for a, d in zip(g_b, gs))
+    del wsgs
+    # the batched gradient with every shot's D kept in HBM (ckpt_every = nt)
+    keep = None
+    need = F.batched_gradient_workspace_size(gs, nt)
+    torch.cuda.empty_cache()
+    if need + (4 << 30) < torch.cuda.mem_get_info()[0]:
+        wsk = F.workspace(need, dev)
+        kms = best(lambda: F.fd_adjoint_gradient_batched(gs, nt, wsk))
+        del wsk
+        keep = {"batched_gpts": sum(pts[:len(gs)]) * nt / (kms * 1e-3) / 1e9, "batched_ms": kms,
+                "workspace_gb": need / 1e9,
+                "bitwise_equal": all(torch.equal(a, d["grad"]) for a, d in zip(g_b, gs))}
     work = sum(pts) * nt
     gwork = sum(pts[:len(gs)]) * nt
     return {"forward": {"shots": len(shots), "batched_gpts": work / (ms_b * 1e-3) / 1e9,
@@ -674,7 +686,7 @@ def batched_vs_single(args, dev, stream, shots, grad_shots=8, k=GRAD_K):
                          "batched_gpts": gwork / (gms_b * 1e-3) / 1e9,
                          "single_shot_gpts": gwork / (gms_s * 1e-3) / 1e9, "batched_ms": gms_b,
                          "single_shot_ms": gms_s, "speedup": gms_s / gms_b,
-                         "bitwise_equal": same_grad},
+                         "bitwise_equal": same_grad, "keep_all_d": keep},
             "note": "gradient points per second count padded points x time steps of the "
                     "gradient (its three sweeps)"}
 
