@@ -493,7 +493,9 @@ def _make_traces_fn():
 
     class AcousticTraces(torch.autograd.Function):
         """traces = F(m); grad_m = F'(m)^T grad_traces via fd_adjoint_gradient
-        (checkpoints every ``k`` steps, segments recomputed)."""
+        (checkpoints every ``k`` steps, segments recomputed; ``k = None`` keeps
+        every step's D when the device has room for it, else k = 20; the
+        gradient is bitwise the same for every k)."""
 
         @staticmethod
         def forward(ctx, m, plan, src_idx, wavelet, rec_idx, k):
@@ -512,10 +514,14 @@ def _make_traces_fn():
             m, wavelet = ctx.saved_tensors
             plan = ctx.plan
             grad = torch.empty_like(m)
-            ws = workspace(plan.gradient_workspace_size(len(ctx.src_idx), len(ctx.rec_idx), ctx.k),
+            k = ctx.k
+            if k is None:
+                need = plan.gradient_workspace_size(len(ctx.src_idx), len(ctx.rec_idx), plan.nt)
+                k = plan.nt if need + (4 << 30) < torch.cuda.mem_get_info(m.device)[0] else 20
+            ws = workspace(plan.gradient_workspace_size(len(ctx.src_idx), len(ctx.rec_idx), k),
                            m.device)
             fd_adjoint_gradient(plan, m, ctx.src_idx, wavelet, ctx.rec_idx,
-                                grad_traces.contiguous().float(), ctx.k, grad, ws,
+                                grad_traces.contiguous().float(), k, grad, ws,
                                 model_kind=FD_MODEL_SLOWNESS2)
             check_status(plan, ws, "acoustic_traces backward")
             return grad, None, None, None, None, None
@@ -526,8 +532,10 @@ def _make_traces_fn():
 _traces_fn = None
 
 
-def acoustic_traces(m, plan: Plan, src_idx, wavelet, rec_idx, k: int = 20):
-    """Differentiable traces(m) for m = 1/v^2 on the physical grid."""
+def acoustic_traces(m, plan: Plan, src_idx, wavelet, rec_idx, k=None):
+    """Differentiable traces(m) for m = 1/v^2 on the physical grid.  ``k`` is
+    the backward pass's checkpoint interval; None keeps every step's D in
+    device memory when it fits (no recompute), else checkpoints every 20."""
     global _traces_fn
     if _traces_fn is None:
         _traces_fn = _make_traces_fn()
