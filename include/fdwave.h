@@ -305,6 +305,37 @@ int fd_adjoint_gradient(fd_plan *plan, int model_kind, const float *model_d,
                         float *wavelet_grad_d, void *ws_d, size_t ws_bytes, void *stream);
 
 /*
+ * fd_gradient_forward / fd_gradient_adjoint - fd_adjoint_gradient with
+ * ckpt_every = nt split in two calls, for callers that need the traces before
+ * they can form the residual (a misfit J(d, d_obs), an autograd backward).  No
+ * counterpart in the paper (whose FWI outlook implies the same gradient).
+ * fd_gradient_forward runs the forward sweep, writes the traces (traces_d
+ * optional) and keeps the D field of every step in ws_d;
+ * fd_gradient_adjoint then runs the adjoint sweep from them for a residual and
+ * writes dJ/dm (and dJ/ds if wavelet_grad_d is not NULL).  The forward sweep
+ * is not repeated, so a misfit gradient costs one forward and one adjoint
+ * sweep.  Both calls take the same plan, sources, receivers and workspace,
+ * sized by fd_gradient_workspace_size with ckpt_every = nt; nothing may write
+ * ws_d in between, and fd_gradient_adjoint may be called several times (other
+ * residuals) after one fd_gradient_forward.  The gradient and traces are
+ * bitwise those of fd_adjoint_gradient.  A plan keeps up to 64 stored
+ * forwards (workspace, source and receiver counts), so the forwards of several
+ * shots may precede their adjoints.  Errors: as fd_adjoint_gradient, and
+ * FD_ERR_ARG from fd_gradient_adjoint when no stored forward of the plan has
+ * this workspace and these counts: none was made, another call on the plan
+ * (fd_forward, fd_adjoint_gradient) has since written the workspace, or the
+ * kernel variant changed (fd_plan_set_variant, fd_plan_autotune).
+ */
+int fd_gradient_forward(fd_plan *plan, int model_kind, const float *model_d,
+                        int nsrc, const int64_t *src_idx, const float *wavelet_d,
+                        int nrec, const int64_t *rec_idx, float *traces_d,
+                        void *ws_d, size_t ws_bytes, void *stream);
+int fd_gradient_adjoint(fd_plan *plan, int nsrc, const int64_t *src_idx,
+                        int nrec, const int64_t *rec_idx, const float *resid_d,
+                        float *grad_d, float *wavelet_grad_d,
+                        void *ws_d, size_t ws_bytes, void *stream);
+
+/*
  * Batched shots (no counterpart in the paper, whose experiments run one
  * source at a time): independent forward problems, possibly on grids of
  * different size, with the same stencil, dt and nt, advanced together.  For

@@ -100,6 +100,8 @@ _SIGS = {
     "fd_status_read": (_I, [_P, _P, _P]),
     "fd_gradient_workspace_size": (_I, [_P, _I, _I, _I, _P]),
     "fd_adjoint_gradient": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _I, _P, _P, _P, _P, _SZ, _P]),
+    "fd_gradient_forward": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _P, _P, _SZ, _P]),
+    "fd_gradient_adjoint": (_I, [_P, _I, _P, _I, _P, _P, _P, _P, _P, _SZ, _P]),
     "fd_forward_batched_workspace_size": (_I, [_I, _P, _P]),
     "fd_forward_batched": (_I, [_I, _P, _P, _SZ, _P]),
     "fd_forward_batched_autotune": (_I, [_I, _P, _P, _SZ, _P]),
@@ -403,6 +405,31 @@ def fd_adjoint_gradient(plan: Plan, model, src_idx, wavelet, rec_idx, resid, k: 
                                      _addr(ws), ws.numel(), _stream_ptr(stream)))
 
 
+def fd_gradient_forward(plan: Plan, model, src_idx, wavelet, rec_idx, traces, ws,
+                        model_kind: int = FD_MODEL_VELOCITY, stream=None):
+    """Forward sweep of the gradient keeping every step's D in ws (sized by
+    plan.gradient_workspace_size(nsrc, nrec, plan.nt))."""
+    src_idx = np.ascontiguousarray(src_idx, np.int64)
+    rec_idx = np.ascontiguousarray(rec_idx, np.int64)
+    _check(lib().fd_gradient_forward(plan.ptr, model_kind, _addr(model), len(src_idx),
+                                     src_idx.ctypes.data if len(src_idx) else None,
+                                     _addr(wavelet), len(rec_idx),
+                                     rec_idx.ctypes.data if len(rec_idx) else None, _addr(traces),
+                                     _addr(ws), ws.numel(), _stream_ptr(stream)))
+
+
+def fd_gradient_adjoint(plan: Plan, src_idx, rec_idx, resid, grad, ws, wavelet_grad=None,
+                        stream=None):
+    """Adjoint sweep after fd_gradient_forward on the same plan and ws."""
+    src_idx = np.ascontiguousarray(src_idx, np.int64)
+    rec_idx = np.ascontiguousarray(rec_idx, np.int64)
+    _check(lib().fd_gradient_adjoint(plan.ptr, len(src_idx),
+                                     src_idx.ctypes.data if len(src_idx) else None, len(rec_idx),
+                                     rec_idx.ctypes.data if len(rec_idx) else None, _addr(resid),
+                                     _addr(grad), _addr(wavelet_grad), _addr(ws), ws.numel(),
+                                     _stream_ptr(stream)))
+
+
 def fd_forward_batched(shots: Sequence[dict], ws, stream=None):
     """shots: dicts with plan, model, src_idx, wavelet, rec_idx, traces
     (and optional model_kind)."""
@@ -492,19 +519,32 @@ def _make_traces_fn():
     torch = _torch()
 
     class AcousticTraces(torch.autograd.Function):
-        """traces = F(m); grad_m = F'(m)^T grad_traces via fd_adjoint_gradient
-        (checkpoints every ``k`` steps, segments recomputed; ``k = None`` keeps
-        every step's D when the device has room for it, else k = 20; the
-        gradient is bitwise the same for every k)."""
+        """traces = F(m); grad_m = F'(m)^T grad_traces by the discrete adjoint.
+        ``k = None``: when the device has room for every step's D, the forward
+        keeps them (fd_gradient_forward) and the backward runs only the
+        adjoint sweep (fd_gradient_adjoint); else the backward calls
+        fd_adjoint_gradient with checkpoints every 20 steps.  An integer ``k``
+        always takes the second path with that interval.  The gradient is
+        bitwise the same either way."""
 
         @staticmethod
         def forward(ctx, m, plan, src_idx, wavelet, rec_idx, k):
             nt = plan.nt
             traces = torch.empty((nt, len(rec_idx)), dtype=torch.float32, device=m.device)
-            ws = workspace(plan.forward_workspace_size(len(src_idx), len(rec_idx)), m.device)
-            fd_forward(plan, m, src_idx, wavelet, rec_idx, traces, ws,
-                       model_kind=FD_MODEL_SLOWNESS2)
-            check_status(plan, ws, "acoustic_traces forward")
+            ctx.store = None
+            if k is None:
+                need = plan.gradient_workspace_size(len(src_idx), len(rec_idx), nt)
+                if need + (4 << 30) < torch.cuda.mem_get_info(m.device)[0]:
+                    ws = workspace(need, m.device)
+                    fd_gradient_forward(plan, m, src_idx, wavelet, rec_idx, traces, ws,
+                                        model_kind=FD_MODEL_SLOWNESS2)
+                    check_status(plan, ws, "acoustic_traces forward")
+                    ctx.store = ws
+            if ctx.store is None:
+                ws = workspace(plan.forward_workspace_size(len(src_idx), len(rec_idx)), m.device)
+                fd_forward(plan, m, src_idx, wavelet, rec_idx, traces, ws,
+                           model_kind=FD_MODEL_SLOWNESS2)
+                check_status(plan, ws, "acoustic_traces forward")
             ctx.save_for_backward(m, wavelet)
             ctx.plan, ctx.src_idx, ctx.rec_idx, ctx.k = plan, src_idx, rec_idx, k
             return traces
@@ -514,15 +554,17 @@ def _make_traces_fn():
             m, wavelet = ctx.saved_tensors
             plan = ctx.plan
             grad = torch.empty_like(m)
-            k = ctx.k
-            if k is None:
-                need = plan.gradient_workspace_size(len(ctx.src_idx), len(ctx.rec_idx), plan.nt)
-                k = plan.nt if need + (4 << 30) < torch.cuda.mem_get_info(m.device)[0] else 20
-            ws = workspace(plan.gradient_workspace_size(len(ctx.src_idx), len(ctx.rec_idx), k),
-                           m.device)
-            fd_adjoint_gradient(plan, m, ctx.src_idx, wavelet, ctx.rec_idx,
-                                grad_traces.contiguous().float(), k, grad, ws,
-                                model_kind=FD_MODEL_SLOWNESS2)
+            if ctx.store is not None:
+                ws, ctx.store = ctx.store, None
+                fd_gradient_adjoint(plan, ctx.src_idx, ctx.rec_idx, grad_traces.contiguous().float(),
+                                    grad, ws)
+            else:
+                k = 20 if ctx.k is None else ctx.k
+                ws = workspace(plan.gradient_workspace_size(len(ctx.src_idx), len(ctx.rec_idx), k),
+                               m.device)
+                fd_adjoint_gradient(plan, m, ctx.src_idx, wavelet, ctx.rec_idx,
+                                    grad_traces.contiguous().float(), k, grad, ws,
+                                    model_kind=FD_MODEL_SLOWNESS2)
             check_status(plan, ws, "acoustic_traces backward")
             return grad, None, None, None, None, None
 
@@ -535,7 +577,8 @@ _traces_fn = None
 def acoustic_traces(m, plan: Plan, src_idx, wavelet, rec_idx, k=None):
     """Differentiable traces(m) for m = 1/v^2 on the physical grid.  ``k`` is
     the backward pass's checkpoint interval; None keeps every step's D in
-    device memory when it fits (no recompute), else checkpoints every 20."""
+    device memory from the forward when it fits (the backward then runs only
+    the adjoint sweep), else checkpoints every 20."""
     global _traces_fn
     if _traces_fn is None:
         _traces_fn = _make_traces_fn()

@@ -34,8 +34,22 @@ struct fd_plan {
     float gcoef = 0.f;
     float W[fdw::kWDim * fdw::kWDim];
     void *last_ws = nullptr;
+    // (workspace, source count, receiver count) of the recent
+    // fd_gradient_forward calls, newest last: the states fd_gradient_adjoint
+    // accepts (cleared when the kernel variant changes)
+    std::vector<std::pair<void *, std::pair<int, int>>> stores;
     uint64_t id = 0;   // unique per created plan (never reused: keys the graph cache)
 };
+
+// Forget a workspace as a stored forward (another call is about to write it)
+static void forget_store(fd_plan *p, void *ws)
+{
+    for (size_t i = 0; i < p->stores.size(); ++i)
+        if (p->stores[i].first == ws) {
+            p->stores.erase(p->stores.begin() + (long)i);
+            return;
+        }
+}
 
 namespace fdw {
 
@@ -574,6 +588,7 @@ extern "C" int fd_plan_autotune(fd_plan *p, int model_kind, const float *model, 
 {
     clear_error();
     if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
+    p->stores.clear();   // a stored forward's tables belong to the old variant
     size_t need = make_layout(p, 0, 0, false, 1).total;
     // variants with more tiles need larger tables: size for the worst case
     need += 4 * kAlign;
@@ -693,6 +708,7 @@ extern "C" int fd_plan_set_variant(fd_plan *p, int variant, int z_chunk)
     clear_error();
     if (!p || z_chunk < 0) return set_error(FD_ERR_ARG, "bad argument");
     if (p->var.generic) return set_error(FD_ERR_UNSUPPORTED, "the generic kernel has no variants");
+    p->stores.clear();   // a stored forward's tables belong to the old variant
     int prefs[kMaxVariants];
     const int np = p->prob.dim == 2 ? variants_2d(p->shape_eff, p->st.M, prefs, kMaxVariants)
                                     : variants_3d(p->shape_eff, p->st.M, prefs, kMaxVariants);
@@ -973,6 +989,7 @@ extern "C" int fd_forward(fd_plan *p, int model_kind, const float *model, int ns
                           size_t ws_bytes, void *stream)
 {
     clear_error();
+    if (p) forget_store(p, ws);
     return forward_impl(p, model_kind, model, nsrc, src, wavelet, nrec, rec, traces, state_in_d,
                         state_out_d, ws, ws_bytes, stream, true);
 }
@@ -997,39 +1014,42 @@ extern "C" int fd_status_read(const fd_plan *p, void *ws, void *stream)
     return FD_OK;
 }
 
-extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *model, int nsrc,
-                                   const int64_t *src, const float *wavelet, int nrec,
-                                   const int64_t *rec, const float *resid, int k, float *grad,
-                                   float *traces, float *wavelet_grad, void *ws, size_t ws_bytes,
-                                   void *stream)
+namespace {
+
+// The checkpointed gradient in two phases: kGradForward sets the workspace up
+// (tables, maps, kappa, cleared buffers) and runs the forward sweep; kGradAdjoint
+// runs the backward sweep (restore and recompute per segment, unless one
+// segment holds every D) and the fold.  fd_adjoint_gradient runs both;
+// fd_gradient_forward and fd_gradient_adjoint run one each with k = nt.
+constexpr int kGradForward = 1, kGradAdjoint = 2;
+
+int gradient_run(fd_plan *p, int model_kind, const float *model, int nsrc, const int64_t *src,
+                 const float *wavelet, int nrec, const int64_t *rec, const float *resid, int k,
+                 float *grad, float *traces, float *wavelet_grad, void *ws, size_t ws_bytes,
+                 void *stream, int phases)
 {
-    clear_error();
-    if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
-    if (k < 1) return set_error(FD_ERR_ARG, "ckpt_every must be >= 1");
     const int nt = p->prob.nt;
-    k = std::min(k, std::max(nt, 1));
     const Layout L = make_layout(p, nsrc, nrec, true, k);
-    int st = check_common(p, model_kind, model, nsrc, src, wavelet, nrec, rec, ws, ws_bytes, L.total);
-    if (st) return st;
-    if (!grad) return set_error(FD_ERR_ARG, "grad is NULL");
-    if (nrec > 0 && !resid) return set_error(FD_ERR_ARG, "resid is NULL");
-    if ((st = ensure_tuned(p))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *w = reinterpret_cast<char *>(ws);
+    int st = 0;
     Tables T;
     if ((st = make_tables(p, nsrc, src, nrec, rec, true, T))) return st;
-    if ((st = upload_tables(p, L, w, T, s))) return st;
-    if ((st = upload_maps(p, L, w, 4, s))) return st;
-    FDW_CK(cudaMemsetAsync(w + L.status, 0, kAlign, s));
     const size_t fb = up((size_t)p->field * sizeof(float));
     float *buf[4];
-    for (int i = 0; i < 4; ++i) {
-        buf[i] = reinterpret_cast<float *>(w + L.buf[i]);
-        FDW_CK(cudaMemsetAsync(buf[i], 0, fb, s));
-    }
+    for (int i = 0; i < 4; ++i) buf[i] = reinterpret_cast<float *>(w + L.buf[i]);
     float *gacc = reinterpret_cast<float *>(w + L.gacc);
-    FDW_CK(cudaMemsetAsync(gacc, 0, fb, s));
-    if ((st = prep_model(p, L, w, model_kind, model, s))) return st;
+    if (phases & kGradForward) {
+        if ((st = upload_tables(p, L, w, T, s))) return st;
+        if ((st = upload_maps(p, L, w, 4, s))) return st;
+        FDW_CK(cudaMemsetAsync(w + L.status, 0, kAlign, s));
+        for (int i = 0; i < 2; ++i) FDW_CK(cudaMemsetAsync(buf[i], 0, fb, s));
+        if ((st = prep_model(p, L, w, model_kind, model, s))) return st;
+    }
+    if (phases & kGradAdjoint) {   // cleared here, so one stored forward serves several adjoints
+        for (int i = 2; i < 4; ++i) FDW_CK(cudaMemsetAsync(buf[i], 0, fb, s));
+        FDW_CK(cudaMemsetAsync(gacc, 0, fb, s));
+    }
     const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(w + L.tmaps);
     char *ck = w + L.ckpt;
     char *dseg = w + L.dseg;
@@ -1057,7 +1077,7 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
     const bool store_all = L.nck == 1;
     // forward sweep with checkpoints (u^n, u^{n-1}) at n = s k
     bind_fwd(true);
-    for (int n = 0; n < nt; ++n) {
+    for (int n = 0; n < ((phases & kGradForward) ? nt : 0); ++n) {
         const int cur = n & 1;
         if (n % k == 0 && !store_all) {
             const int c = n / k;
@@ -1073,6 +1093,7 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
         FDW_CK(launch(p, store_all ? kModeStoreD : kModeForward, sp, s));
     }
     sp.dseg_out = nullptr;
+    if (!(phases & kGradAdjoint)) return FD_OK;
     // backward sweep over segments
     int t = 0;   // adjoint steps done: q^{j+1} lives in buf[2 + (t & 1)]
     for (int c = L.nck - 1; c >= 0; --c) {
@@ -1119,6 +1140,79 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
     const int64_t phys[3] = {pr.n[0], pr.n[1], pr.n[2]};
     FDW_CK(launch_fold_grad(gacc, p->pitch, zstride(p), phys, pr.nb, (float)(-1.0 / (pr.dt * pr.dt)),
                             grad, s));
+    return FD_OK;
+}
+
+}  // namespace
+
+extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *model, int nsrc,
+                                   const int64_t *src, const float *wavelet, int nrec,
+                                   const int64_t *rec, const float *resid, int k, float *grad,
+                                   float *traces, float *wavelet_grad, void *ws, size_t ws_bytes,
+                                   void *stream)
+{
+    clear_error();
+    if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
+    if (k < 1) return set_error(FD_ERR_ARG, "ckpt_every must be >= 1");
+    k = std::min(k, std::max(p->prob.nt, 1));
+    const Layout L = make_layout(p, nsrc, nrec, true, k);
+    int st = check_common(p, model_kind, model, nsrc, src, wavelet, nrec, rec, ws, ws_bytes, L.total);
+    if (st) return st;
+    if (!grad) return set_error(FD_ERR_ARG, "grad is NULL");
+    if (nrec > 0 && !resid) return set_error(FD_ERR_ARG, "resid is NULL");
+    if ((st = ensure_tuned(p))) return st;
+    forget_store(p, ws);
+    st = gradient_run(p, model_kind, model, nsrc, src, wavelet, nrec, rec, resid, k, grad, traces,
+                      wavelet_grad, ws, ws_bytes, stream, kGradForward | kGradAdjoint);
+    if (st) return st;
+    p->last_ws = ws;
+    return FD_OK;
+}
+
+extern "C" int fd_gradient_forward(fd_plan *p, int model_kind, const float *model, int nsrc,
+                                   const int64_t *src, const float *wavelet, int nrec,
+                                   const int64_t *rec, float *traces, void *ws, size_t ws_bytes,
+                                   void *stream)
+{
+    clear_error();
+    if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
+    const int k = std::max(p->prob.nt, 1);
+    const Layout L = make_layout(p, nsrc, nrec, true, k);
+    int st = check_common(p, model_kind, model, nsrc, src, wavelet, nrec, rec, ws, ws_bytes, L.total);
+    if (st) return st;
+    if ((st = ensure_tuned(p))) return st;
+    forget_store(p, ws);
+    st = gradient_run(p, model_kind, model, nsrc, src, wavelet, nrec, rec, nullptr, k, nullptr, traces,
+                      nullptr, ws, ws_bytes, stream, kGradForward);
+    if (st) return st;
+    p->stores.push_back({ws, {nsrc, nrec}});
+    if (p->stores.size() > 64) p->stores.erase(p->stores.begin());
+    p->last_ws = ws;
+    return FD_OK;
+}
+
+extern "C" int fd_gradient_adjoint(fd_plan *p, int nsrc, const int64_t *src, int nrec,
+                                   const int64_t *rec, const float *resid, float *grad,
+                                   float *wavelet_grad, void *ws, size_t ws_bytes, void *stream)
+{
+    clear_error();
+    if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
+    bool known = false;
+    for (const auto &e : p->stores)
+        known = known || (e.first == ws && e.second.first == nsrc && e.second.second == nrec);
+    if (!ws || !known)
+        return set_error(FD_ERR_ARG, "no fd_gradient_forward of this plan with this workspace and "
+                         "these source and receiver counts precedes the call");
+    if (nsrc < 0 || nrec < 0 || (nsrc > 0 && !src) || (nrec > 0 && !rec))
+        return set_error(FD_ERR_ARG, "bad source or receiver arguments");
+    const int k = std::max(p->prob.nt, 1);
+    const Layout L = make_layout(p, nsrc, nrec, true, k);
+    if (ws_bytes < L.total) return set_error(FD_ERR_NOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+    if (!grad) return set_error(FD_ERR_ARG, "grad is NULL");
+    if (nrec > 0 && !resid) return set_error(FD_ERR_ARG, "resid is NULL");
+    int st = gradient_run(p, FD_MODEL_VELOCITY, nullptr, nsrc, src, nullptr, nrec, rec, resid, k, grad,
+                          nullptr, wavelet_grad, ws, ws_bytes, stream, kGradAdjoint);
+    if (st) return st;
     p->last_ws = ws;
     return FD_OK;
 }

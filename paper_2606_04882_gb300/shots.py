@@ -85,13 +85,37 @@ def misfit_and_gradient(template, nshots: int,
 
 
 def gpu_shot_fn(plan, model_m, src_idx: Sequence[np.ndarray], wavelets, rec_idx: np.ndarray,
-                d_obs, k: int = 20):
+                d_obs, k=None):
     """Per-shot (J_s, dJ/dm) on the GPU for m = 1/v^2: forward traces, residual
-    d - d_obs, adjoint gradient with checkpoints every k steps."""
+    d - d_obs, adjoint gradient.  k = None: when every step's D fits the
+    device, one forward sweep keeps them (fd_gradient_forward) and the adjoint
+    runs from them (fd_gradient_adjoint); else, or with an integer k, a plain
+    forward for the traces and fd_adjoint_gradient with checkpoints every k
+    (20 by default) steps.  The results are bitwise the same."""
     import torch
-    from . import FD_MODEL_SLOWNESS2, check_status, fd_adjoint_gradient, fd_forward, workspace
+    from . import (FD_MODEL_SLOWNESS2, check_status, fd_adjoint_gradient, fd_forward,
+                   fd_gradient_adjoint, fd_gradient_forward, workspace)
     dev = model_m.device
     nrec = len(rec_idx)
+    if k is None:
+        need = plan.gradient_workspace_size(1, nrec, plan.nt)
+        if need + (4 << 30) < torch.cuda.mem_get_info(dev)[0]:
+            wss = workspace(need, dev)
+
+            def run_split(s):
+                tr = torch.empty((plan.nt, nrec), device=dev)
+                fd_gradient_forward(plan, model_m, src_idx[s], wavelets[s], rec_idx, tr, wss,
+                                    model_kind=FD_MODEL_SLOWNESS2)
+                check_status(plan, wss, "forward of shot %d" % s)
+                r = tr - d_obs[s]
+                J = 0.5 * float((r.double() ** 2).sum())
+                g = torch.empty_like(model_m)
+                fd_gradient_adjoint(plan, src_idx[s], rec_idx, r, g, wss)
+                check_status(plan, wss, "gradient of shot %d" % s)
+                return J, g
+
+            return run_split
+        k = 20
     wsf = workspace(plan.forward_workspace_size(1, nrec), dev)
     wsg = workspace(plan.gradient_workspace_size(1, nrec, k), dev)
 

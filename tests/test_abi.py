@@ -147,6 +147,19 @@ def test_workspace_sizes():
     assert p.gradient_workspace_size(1, 100, 5) > g
 
 
+def test_gradient_adjoint_needs_a_stored_forward():
+    """fd_gradient_adjoint checks, before touching the device, that the plan has
+    a stored forward for this workspace and these counts."""
+    d = F.stencil_desc(2, "cross", 4)
+    p = F.Plan((30, 40), 10.0, 1e-3, 20, 6, 3000.0, d)
+    ws = np.zeros(256, np.uint8)
+    with pytest.raises(F.FdError) as e:
+        F._check(F.lib().fd_gradient_adjoint(p.ptr, 0, None, 0, None, None, ws.ctypes.data, None,
+                                             ws.ctypes.data, ws.nbytes, None))
+    assert e.value.code == F.FD_ERR_ARG
+    assert "fd_gradient_forward" in F.last_error()
+
+
 @pytest.mark.parametrize("M,N", [(2, 1), (4, 2), (6, 3)])
 def test_symbol_positive_stencil_is_rejected(M, N):
     """A stencil whose symbol is positive somewhere (DispTE-CrossSq at C = 0.3)

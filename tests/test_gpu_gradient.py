@@ -104,6 +104,45 @@ def test_checkpoint_interval_is_bitwise_invariant(dim, shape):
         assert np.array_equal(tr1, tr) and np.array_equal(wg1, wg), k
 
 
+@pytest.mark.parametrize("dim,shape", [(2, "cross"), (3, "cross"), (3, "rhombus")])
+def test_split_gradient_equals_one_call(dim, shape):
+    """fd_gradient_forward (forward sweep keeping every D, traces out) then
+    fd_gradient_adjoint (adjoint sweep for a residual) give the traces,
+    gradient and wavelet gradient of fd_adjoint_gradient bit for bit; one
+    stored forward serves two adjoints; two stored forwards on one plan are
+    both usable; a workspace rewritten by fd_forward is refused."""
+    import torch
+    import paper_2606_04882_gb300 as F
+    c = _case(dim, 60, shape=shape)
+    resid = np.random.default_rng(12).standard_normal((c.nt, len(c.rec)))
+    g1, tr1, wg1, rc = _gpu_gradient(c, resid, k=7)
+    assert rc == 0
+    plan = c.plan()
+    dev = torch.device("cuda")
+    m = torch.from_numpy(c.vel).to(dev)
+    wav = torch.from_numpy(c.wavelet32()).to(dev)
+    r = torch.from_numpy(resid.astype(np.float32)).to(dev)
+    si, ri = plan.linear_index(c.src), plan.linear_index(c.rec)
+    need = plan.gradient_workspace_size(len(c.src), len(c.rec), c.nt)
+    wss = [F.workspace(need), F.workspace(need)]
+    for ws in wss:
+        tr = torch.zeros((c.nt, len(c.rec)), device=dev)
+        F.fd_gradient_forward(plan, m, si, wav, ri, tr, ws)
+        assert F.fd_status_read(plan, ws) == 0
+        assert np.array_equal(tr.cpu().numpy(), tr1)
+    for ws in (wss[0], wss[0], wss[1]):
+        g = torch.empty_like(m)
+        wg = torch.zeros((c.nt, len(c.src)), device=dev)
+        F.fd_gradient_adjoint(plan, si, ri, r, g, ws, wavelet_grad=wg)
+        assert F.fd_status_read(plan, ws) == 0
+        assert np.array_equal(g.cpu().numpy(), g1)
+        assert np.array_equal(wg.cpu().numpy(), wg1)
+    F.fd_forward(plan, m, si, wav, ri, torch.zeros((c.nt, len(c.rec)), device=dev), wss[1])
+    with pytest.raises(F.FdError) as e:
+        F.fd_gradient_adjoint(plan, si, ri, r, torch.empty_like(m), wss[1])
+    assert e.value.code == F.FD_ERR_ARG
+
+
 def test_slowness_parameterisation_and_autograd():
     import torch
     import paper_2606_04882_gb300 as F
@@ -161,6 +200,11 @@ def test_shot_driver_on_the_gpu_matches_the_oracle_sum():
     J, g = misfit_and_gradient(m, 3, run)
     assert abs(J - J_o) < 1e-4 * J_o
     assert rel_l2(g.cpu().numpy(), g_o) < 1e-4
+    # the default (every D kept, one forward sweep per shot) gives the same bits
+    run = gpu_shot_fn(plan, m, [plan.linear_index(s) for s in srcs], [wav] * 3,
+                      plan.linear_index(rec), [torch.from_numpy(d.astype(np.float32)).to(dev) for d in dobs])
+    J2, g2 = misfit_and_gradient(m, 3, run)
+    assert J2 == J and torch.equal(g2, g)
 
 
 @pytest.mark.parametrize("shape,M,scheme", [("rhombus", 4, "displs"), ("cross", 4, "spatte")])
