@@ -28,3 +28,23 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    assert cb["cpu"]
+
+
+def test_traffic_figure_is_reported_only_for_the_measured_sources(monkeypatch):
+    """The bench's per-launch DRAM traffic comes from an ncu capture of given
+    kernel sources: it is reported (scaled by the point count) while the
+    sources hash to the recorded digest, and null once they differ."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    h = hashlib.sha256()
+    for rel in bench.TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    monkeypatch.setattr(bench, "TRAFFIC_DIGEST", h.hexdigest())
+    for st, b in bench.TRAFFIC_B_PER_POINT.items():
+        assert bench.traffic_per_launch(st, 1000) == b * 1000
+    assert bench.traffic_per_launch("not_a_stencil", 1000) is None
+    monkeypatch.setattr(bench, "TRAFFIC_DIGEST", "0" * 64)
+    assert bench.traffic_per_launch("rhombus4_displs", 1000) is None
