@@ -441,8 +441,9 @@ extern "C" int fd_plan_create(const fd_problem *prob, const fd_stencil_desc *ste
     if (st) { delete p; return st; }
     const double C = pr.vmax * pr.dt / pr.h;
     if (C > p->cmax * (1.0 + 1e-12)) {
+        const double cmax = p->cmax;
         delete p;
-        return set_error(FD_ERR_UNSTABLE, "Courant number %.6g exceeds the stability limit %.6g", C, p->cmax);
+        return set_error(FD_ERR_UNSTABLE, "Courant number %.6g exceeds the stability limit %.6g", C, cmax);
     }
     // weight table W[p][q] and the effective shape (all-zero off-axis orbits -> cross)
     std::memset(p->W, 0, sizeof p->W);
@@ -473,8 +474,9 @@ extern "C" int fd_plan_create(const fd_problem *prob, const fd_stencil_desc *ste
         p->nz_chunks = 1;
     }
     if (st) {
+        const int shape_eff = p->shape_eff;
         delete p;
-        return set_error(FD_ERR_UNSUPPORTED, "no kernel for shape %d, M %d in %dD", p->shape_eff, M, pr.dim);
+        return set_error(FD_ERR_UNSUPPORTED, "no kernel for shape %d, M %d in %dD", shape_eff, M, pr.dim);
     }
     p->ntiles = p->tiles_x * p->tiles_y;
     p->max_tiles = p->ntiles;
@@ -1025,8 +1027,8 @@ constexpr int kGradForward = 1, kGradAdjoint = 2;
 
 int gradient_run(fd_plan *p, int model_kind, const float *model, int nsrc, const int64_t *src,
                  const float *wavelet, int nrec, const int64_t *rec, const float *resid, int k,
-                 float *grad, float *traces, float *wavelet_grad, void *ws, size_t ws_bytes,
-                 void *stream, int phases)
+                 float *grad, float *traces, float *wavelet_grad, void *ws, void *stream,
+                 int phases)
 {
     const int nt = p->prob.nt;
     const Layout L = make_layout(p, nsrc, nrec, true, k);
@@ -1163,7 +1165,7 @@ extern "C" int fd_adjoint_gradient(fd_plan *p, int model_kind, const float *mode
     if ((st = ensure_tuned(p))) return st;
     forget_store(p, ws);
     st = gradient_run(p, model_kind, model, nsrc, src, wavelet, nrec, rec, resid, k, grad, traces,
-                      wavelet_grad, ws, ws_bytes, stream, kGradForward | kGradAdjoint);
+                      wavelet_grad, ws, stream, kGradForward | kGradAdjoint);
     if (st) return st;
     p->last_ws = ws;
     return FD_OK;
@@ -1183,7 +1185,7 @@ extern "C" int fd_gradient_forward(fd_plan *p, int model_kind, const float *mode
     if ((st = ensure_tuned(p))) return st;
     forget_store(p, ws);
     st = gradient_run(p, model_kind, model, nsrc, src, wavelet, nrec, rec, nullptr, k, nullptr, traces,
-                      nullptr, ws, ws_bytes, stream, kGradForward);
+                      nullptr, ws, stream, kGradForward);
     if (st) return st;
     p->stores.push_back({ws, {nsrc, nrec}});
     if (p->stores.size() > 64) p->stores.erase(p->stores.begin());
@@ -1211,7 +1213,7 @@ extern "C" int fd_gradient_adjoint(fd_plan *p, int nsrc, const int64_t *src, int
     if (!grad) return set_error(FD_ERR_ARG, "grad is NULL");
     if (nrec > 0 && !resid) return set_error(FD_ERR_ARG, "resid is NULL");
     int st = gradient_run(p, FD_MODEL_VELOCITY, nullptr, nsrc, src, nullptr, nrec, rec, resid, k, grad,
-                          nullptr, wavelet_grad, ws, ws_bytes, stream, kGradAdjoint);
+                          nullptr, wavelet_grad, ws, stream, kGradAdjoint);
     if (st) return st;
     p->last_ws = ws;
     return FD_OK;
