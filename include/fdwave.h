@@ -319,10 +319,11 @@ int fd_adjoint_gradient(fd_plan *plan, int model_kind, const float *model_d,
  * ws_d in between, and fd_gradient_adjoint may be called several times (other
  * residuals) after one fd_gradient_forward.  The gradient and traces are
  * bitwise those of fd_adjoint_gradient.  A plan keeps up to 64 stored
- * forwards (workspace, source and receiver counts), so the forwards of several
- * shots may precede their adjoints.  Errors: as fd_adjoint_gradient, and
- * FD_ERR_ARG from fd_gradient_adjoint when no stored forward of the plan has
- * this workspace and these counts: none was made, another call on the plan
+ * forwards (workspace and a hash of the source and receiver indices), so the
+ * forwards of several shots may precede their adjoints.  Errors: as
+ * fd_adjoint_gradient, and FD_ERR_ARG from fd_gradient_adjoint when no stored
+ * forward of the plan has this workspace and these sources and receivers:
+ * none was made, another call on the plan
  * (fd_forward, fd_adjoint_gradient) has since written the workspace, or the
  * kernel variant changed (fd_plan_set_variant, fd_plan_autotune).
  */

@@ -34,12 +34,30 @@ struct fd_plan {
     float gcoef = 0.f;
     float W[fdw::kWDim * fdw::kWDim];
     void *last_ws = nullptr;
-    // (workspace, source count, receiver count) of the recent
+    // (workspace, hash of the source and receiver indices) of the recent
     // fd_gradient_forward calls, newest last: the states fd_gradient_adjoint
     // accepts (cleared when the kernel variant changes)
-    std::vector<std::pair<void *, std::pair<int, int>>> stores;
+    std::vector<std::pair<void *, uint64_t>> stores;
     uint64_t id = 0;   // unique per created plan (never reused: keys the graph cache)
 };
+
+// FNV-1a over the source and receiver counts and indices (host arrays): the
+// identity of a stored forward's point tables
+static uint64_t points_hash(int nsrc, const int64_t *src, int nrec, const int64_t *rec)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](uint64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (v >> (8 * b)) & 0xffu;
+            h *= 1099511628211ull;
+        }
+    };
+    mix((uint64_t)nsrc);
+    for (int i = 0; i < nsrc && src; ++i) mix((uint64_t)src[i]);
+    mix((uint64_t)nrec);
+    for (int i = 0; i < nrec && rec; ++i) mix((uint64_t)rec[i]);
+    return h;
+}
 
 // Forget a workspace as a stored forward (another call is about to write it)
 static void forget_store(fd_plan *p, void *ws)
@@ -1187,7 +1205,7 @@ extern "C" int fd_gradient_forward(fd_plan *p, int model_kind, const float *mode
     st = gradient_run(p, model_kind, model, nsrc, src, wavelet, nrec, rec, nullptr, k, nullptr, traces,
                       nullptr, ws, stream, kGradForward);
     if (st) return st;
-    p->stores.push_back({ws, {nsrc, nrec}});
+    p->stores.push_back({ws, points_hash(nsrc, src, nrec, rec)});
     if (p->stores.size() > 64) p->stores.erase(p->stores.begin());
     p->last_ws = ws;
     return FD_OK;
@@ -1199,14 +1217,14 @@ extern "C" int fd_gradient_adjoint(fd_plan *p, int nsrc, const int64_t *src, int
 {
     clear_error();
     if (!p) return set_error(FD_ERR_ARG, "plan is NULL");
-    bool known = false;
-    for (const auto &e : p->stores)
-        known = known || (e.first == ws && e.second.first == nsrc && e.second.second == nrec);
-    if (!ws || !known)
-        return set_error(FD_ERR_ARG, "no fd_gradient_forward of this plan with this workspace and "
-                         "these source and receiver counts precedes the call");
     if (nsrc < 0 || nrec < 0 || (nsrc > 0 && !src) || (nrec > 0 && !rec))
         return set_error(FD_ERR_ARG, "bad source or receiver arguments");
+    const uint64_t h = points_hash(nsrc, src, nrec, rec);
+    bool known = false;
+    for (const auto &e : p->stores) known = known || (e.first == ws && e.second == h);
+    if (!ws || !known)
+        return set_error(FD_ERR_ARG, "no fd_gradient_forward of this plan with this workspace and "
+                         "these sources and receivers precedes the call");
     const int k = std::max(p->prob.nt, 1);
     const Layout L = make_layout(p, nsrc, nrec, true, k);
     if (ws_bytes < L.total) return set_error(FD_ERR_NOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
