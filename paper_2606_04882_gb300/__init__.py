@@ -532,7 +532,7 @@ def _make_traces_fn():
             nt = plan.nt
             traces = torch.empty((nt, len(rec_idx)), dtype=torch.float32, device=m.device)
             ctx.store = None
-            if k is None:
+            if k is None and ctx.needs_input_grad[0]:
                 need = plan.gradient_workspace_size(len(src_idx), len(rec_idx), nt)
                 if need + (4 << 30) < torch.cuda.mem_get_info(m.device)[0]:
                     ws = workspace(need, m.device)
